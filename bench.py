@@ -1,0 +1,392 @@
+"""Benchmark: reaction events per second of the ensemble workload on GB300.
+
+Workload (one step): the Lotka-Volterra predator-prey model of Table 4
+(c = 10, 0.01, 10; X0 = Y0 = 1000), birth-death (0 -> A at 100, A -> 0 at 1,
+A0 = 0) and dimerisation (2A -> B at 0.001, B -> 2A at 0.1, A0 = 1000), each
+2^20 trajectories to t_end = 10, one thread per trajectory, Philox seed 1,
+ensemble moments of X on a 0.01 grid plus final states.  Step i simulates the
+trajectory ids [i * 2^20, (i+1) * 2^20) of each network.
+
+Printed JSON: value = events/s of the whole job (sum over ranks of fired
+events / max over ranks of the timed device time); e2e = the same metric through
+api.simulate with inputs copied from pinned host memory and outputs copied back
+inside the timed region; roofline for the dominant kernel (the Lotka-Volterra
+launch, FP64-pipe bound); cpu_baseline = the CPU oracle on the host cores over a
+bounded sample of the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--traj N]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2103_00405_gb300 import workloads as W  # noqa: E402
+
+METRIC = "reaction events/s on 1 GB300 (plain, batched, +grad) and % of roofline"
+UNIT = "events/s"
+SAMPLE_DT = 0.01
+# FP64 issue rate: nominal 1.25 TFLOP/s counts an FMA as 2 flops, so single adds,
+# multiplies, divides and conversions retire at most 0.625e12 per second.
+FP64_OP_PEAK = 0.625e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--traj", type=int, default=1 << 20, help="trajectories per network per step")
+    ap.add_argument("--cpu-sample", type=int, default=1024, help="oracle trajectories per network")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--t-end", type=float, default=10.0, help="horizon (reduced only for profiling captures)")
+    ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg (profiling captures)")
+    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "large"],
+                    help="ensemble (default): LV + birth-death + dimerisation; large: N=1e4, M=1e6, 16 trajectories")
+    ap.add_argument("--events", type=int, default=100_000, help="large workload: events per trajectory per step")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        loaded = [s for s in sm if smax and s > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def fp64_ops_per_event(net, counts):
+    """Algorithmic binary64 operations of the events (Table 2 with Eq. 17, 25):
+    per event, per channel: P-T, /a, a*dt, T+ (4); plus t+dt and P_mu+E (2); plus a
+    conversion and a multiply for every propensity the fired channel's dependency
+    list recomputes.  counts: [M] total firings per channel over the launch."""
+    S = net.dense_reactants()
+    V = net.dense_stoich()
+    M = net.n_reactions
+    changed = V != 0
+    reads = S > 0
+    deps = np.array([int((reads[:, changed[k]].any(1)).sum()) for k in range(M)])
+    n = counts.sum()
+    return float(n * (4 * M + 2) + 2 * (counts * deps).sum()), float(n)
+
+
+def cpu_baseline(cfgs, sample):
+    import oracle
+    threads = os.cpu_count() or 1
+    ev, t0 = 0, time.perf_counter()
+    for c in cfgs:
+        o = oracle.run(c["net"], c["x0"], c["t_end"], sample, seed=c["seed"], max_events=c["max_events"],
+                       n_threads=threads)
+        ev += int(o["n_events"].sum())
+    dt = time.perf_counter() - t0
+    return {"value": ev / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d trajectories of each of the 3 networks to t_end=10 (%d events, %.1f s)" % (sample, ev, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cfgs = W.ensemble_configs(args.traj)
+    sample = args.cpu_sample
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state
+    vals, times = [], []
+    for _ in range(args.steps):
+        b = cpu_baseline(cfgs, sample)
+        vals.append(b["value"])
+    b["value"] = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "ensemble: Lotka-Volterra + birth-death + dimerisation, CPU oracle sample",
+                       "trajectories_per_network": sample, "t_end": 10.0, "seed": 1},
+            "cpu_baseline": b, "e2e": {"value": b["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                       "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def hbm_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_large(args):
+    """Large-network mode: N = 1e4 species, M = 1e6 reactions, 16 trajectories, `--events` events each
+    per step (t_end = inf), a bundle of blocks per trajectory streaming P, T, a through HBM."""
+    import torch
+
+    from paper_2103_00405_gb300 import _lib as L
+    from paper_2103_00405_gb300 import api
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = W.large_network_config(max_events=args.events)
+    net, n_traj, M = cfg["net"], cfg["n_traj"], cfg["net"].n_reactions
+    netg = api.Network(net)
+    x0 = torch.as_tensor(cfg["x0"], dtype=torch.int32).to(dev)
+    stream = torch.cuda.current_stream()
+    outs = {}
+
+    def step(i, ev=None):
+        a = b = None
+        if ev is not None:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        o = api.simulate(netg, x0, math.inf, n_traj, seed=1, traj_offset=(rank * 1000 + i) * n_traj,
+                         max_events=args.events, mapping=L.RT_MAP_BUNDLE, outputs=outs)
+        outs.update(o)
+        if ev is not None:
+            b.record(stream)
+            ev.append((a, b))
+
+    for i in range(args.warmup):
+        step(100 + i)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    evts, total = [], 0
+    for i in range(args.steps):
+        step(i, evts)
+        total += int(outs["n_events"].sum().item())
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = [a.elapsed_time(b) for a, b in evts]
+    dev_ms = sum(ms)
+    value = total / (dev_ms / 1e3)
+    peak, how = hbm_peak_gbs()
+    per_launch_events = total / args.steps
+    achieved = 32.0 * M * per_launch_events / (statistics.mean(ms) / 1e3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "large network: random mass-action N=1e4, M=1e6 uni/bimolecular, c~lognormal(0,1), "
+                                   "X0~Poisson(100), 16 trajectories, bundle of blocks per trajectory",
+                       "events_per_trajectory_per_step": args.events, "t_end": "inf", "seed": 1,
+                       "l2": "inputs larger than L2 (16 x 24 MB of P, T, a streamed per event)"},
+            "clocks": clocks, "gpu_launches": 2 * len(evts),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_bundle",
+                         "bytes_per_channel_event": 32, "peak_source": how}}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.workload == "large":
+        return run_large(args)
+
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2103_00405_gb300 import _lib as L
+    from paper_2103_00405_gb300 import api
+
+    dev = torch.device("cuda", local)
+    n = args.traj
+    cfgs = W.ensemble_configs(n)
+    for c in cfgs:
+        c["t_end"] = args.t_end
+    nets = [api.Network(c["net"]) for c in cfgs]
+    G = api.grid_len(args.t_end, SAMPLE_DT)
+    outs = []
+    for c in cfgs:
+        N = c["net"].n_species
+        outs.append(dict(x_final=torch.empty((n, N), dtype=torch.int32, device=dev),
+                         n_events=torch.empty(n, dtype=torch.int64, device=dev),
+                         status=torch.empty(n, dtype=torch.int32, device=dev),
+                         t_last=torch.empty(n, dtype=torch.float64, device=dev),
+                         grid_sum=torch.zeros((G, N), dtype=torch.int64, device=dev),
+                         grid_sumsq=torch.zeros((G, N), dtype=torch.int64, device=dev),
+                         grid_count=torch.zeros(G, dtype=torch.int64, device=dev)))
+    x0s = [torch.as_tensor(c["x0"], dtype=torch.int32).to(dev) for c in cfgs]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step(i, timed_events=None):
+        base = (rank * 1000 + i) * n  # disjoint trajectory ids per step and rank
+        for k, c in enumerate(cfgs):
+            for key in ("grid_sum", "grid_sumsq", "grid_count"):
+                outs[k][key].zero_()
+            e0 = e1 = None
+            if timed_events is not None:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            api.simulate(nets[k], x0s[k], c["t_end"], n, seed=c["seed"], traj_offset=base, sample_dt=SAMPLE_DT,
+                         max_events=c["max_events"], grid="moments", mapping=L.RT_MAP_THREAD, outputs=outs[k])
+            if timed_events is not None:
+                e1.record(stream)
+                timed_events.append((k, e0, e1))
+
+    for i in range(args.warmup):
+        step(100 + i)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    evts = []
+    total_events = 0
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)  # evict L2 between timed steps (not inside the timed spans)
+        step(i, evts)
+        total_events += sum(int(o["n_events"].sum().item()) for o in outs)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    per_launch = [(k, a.elapsed_time(b)) for k, a, b in evts]
+    dev_ms = sum(ms for _, ms in per_launch)
+    if world > 1:
+        t = torch.tensor([dev_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ev_t = torch.tensor([float(total_events)], device=dev)
+        torch.distributed.all_reduce(ev_t)
+        dev_ms, total_events = t.item(), int(ev_t.item())
+    value = total_events / (dev_ms / 1e3)
+
+    # dominant kernel: the Lotka-Volterra launch; its algorithmic FP64 ops from the firing counts
+    lv_ms = [ms for k, ms in per_launch if k == 0]
+    lv_launch_ms = statistics.mean(lv_ms)
+    netc = api.Network(cfgs[0]["net"])
+    # firing mix of the last timed Lotka-Volterra launch from its first n/16 trajectories (same ids)
+    chk = api.simulate(netc, x0s[0], args.t_end, max(1, n // 16), seed=1,
+                       traj_offset=(rank * 1000 + args.steps - 1) * n, grad=True, mapping=L.RT_MAP_THREAD,
+                       max_events=cfgs[0]["max_events"])
+    counts = chk["counts"].sum(0, dtype=torch.int64).cpu().numpy()
+    ops_s, ev_s = fp64_ops_per_event(cfgs[0]["net"], counts)
+    lv_last_events = int(outs[0]["n_events"].sum().item())
+    ops = ops_s / ev_s * lv_last_events
+    lv_events = lv_last_events
+    achieved = ops / (lv_ms[-1] / 1e3) / 1e12
+
+    # end to end through the public API: pinned host inputs in, results back to pinned host memory
+    x0_host = [torch.as_tensor(c["x0"], dtype=torch.int32).pin_memory() for c in cfgs]
+    host_out = [{k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
+                 for k, v in o.items() if k in ("x_final", "n_events", "status", "grid_sum", "grid_sumsq",
+                                                "grid_count")} for o in outs]
+    h2d = sum(x.numel() * x.element_size() for x in x0_host)
+    d2h = sum(v.numel() * v.element_size() for ho in host_out for v in ho.values())
+    e2e_ms, e2e_events = 0.0, 0
+    for i in range(0 if args.skip_e2e else args.steps):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for k, c in enumerate(cfgs):
+            xd = x0_host[k].to(dev, non_blocking=True)
+            for key in ("grid_sum", "grid_sumsq", "grid_count"):
+                outs[k][key].zero_()
+            api.simulate(nets[k], xd, c["t_end"], n, seed=c["seed"], traj_offset=(rank * 1000 + 50 + i) * n,
+                         sample_dt=SAMPLE_DT, max_events=c["max_events"], grid="moments", mapping=L.RT_MAP_THREAD,
+                         outputs=outs[k])
+            for key, hv in host_out[k].items():
+                hv.copy_(outs[k][key], non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms += a.elapsed_time(b)
+        e2e_events += sum(int(ho["n_events"].sum()) for ho in host_out)
+    e2e_value = e2e_events / (e2e_ms / 1e3) if e2e_ms > 0 else None
+    if world > 1 and e2e_ms > 0:
+        t = torch.tensor([e2e_ms, float(e2e_events)], device=dev)
+        torch.distributed.all_reduce(t)  # events summed; time summed then divided below
+        e2e_value = t[1].item() / (t[0].item() / world / 1e3)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "ensemble: Lotka-Volterra (Table 4, X0=Y0=1000) + birth-death (k=100, gamma=1) "
+                                   "+ dimerisation (0.001/0.1, A0=1000), 2^20 trajectories each, t_end=10, "
+                                   "one thread per trajectory",
+                       "trajectories_per_network": n, "t_end": args.t_end, "sample_dt": SAMPLE_DT, "seed": 1,
+                       "max_events_per_trajectory": cfgs[0]["max_events"],
+                       "parallelism": "trajectories sharded over ranks" if world > 1 else "1 GPU",
+                       "l2": "flushed between timed steps (512 MB write)",
+                       "events_per_step": total_events / args.steps},
+            "clocks": clocks,
+            "gpu_launches": len(evts),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_OP_PEAK / 1e12, "unit": "TFLOP/s",
+                         "frac": achieved * 1e12 / FP64_OP_PEAK, "traffic": None,
+                         "kernel": "k_ens_thread (Lotka-Volterra launch)", "launch_ms": lv_ms[-1],
+                         "fp64_ops_per_event": ops / lv_events,
+                         "peak_note": "FP64 pipe: nominal 1.25 TFLOP/s with FMA=2 -> 0.625e12 single ops/s (fallback)"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(cfgs, args.cpu_sample)
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * randtime.h -- C ABI of librandtime: GPU (sm_103a) exact stochastic simulation of
+ * chemical reaction networks with the next reaction random time algorithm (NRRTA)
+ * of Liu & Wang, "Parallel implementations of random time algorithm for chemical
+ * network stochastic simulations", arXiv:2103.00405.
+ *
+ * Method (the paper's Sec. 2-4):
+ *   a_k = c_k h_k(X), h_k = prod_j binom(X_j, sigma_jk)                    Eq. 1-2
+ *   X(t) = X(0) + sum_k Y_k(T_k(t)) v_k,  T_k(t) = int_0^t a_k ds           Eq. 16-18
+ *   each channel's next firing internal time P_k is a sum of Exp(1)
+ *   increments ln(1/r) (Eq. 24); its real waiting time is
+ *   dt_k = (P_k - T_k) / a_k (Eq. 25); the smallest fires (Eq. 26); only the
+ *   fired channel draws a new increment (Eq. 27, Table 2).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_dev are device pointers (cudaMalloc / torch CUDA tensors)
+ *     owned by the caller; other pointers are host pointers owned by the caller.
+ *     The library owns only the opaque rt_network / rt_batch objects.
+ *   - Work is enqueued asynchronously on the CUDA stream `stream` (a cudaStream_t;
+ *     NULL = legacy default stream).  Argument errors are detected on the host
+ *     before anything is enqueued and returned as a negative rt_status; the message
+ *     is available from rt_last_error() (thread-local).
+ *   - Per-trajectory outcomes (including numerical overflow) are reported through
+ *     the `status` output, never by trapping.
+ *   - Counts are int32, times binary64.  All floating-point operations on the
+ *     simulation path are single IEEE binary64 operations rounded to nearest, in a
+ *     fixed order, so results are bit-identical for a given (network, inputs, seed)
+ *     regardless of launch configuration.
+ */
+#ifndef RANDTIME_H
+#define RANDTIME_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+typedef enum {
+  RT_OK = 0,
+  RT_ERR_INVALID_ARG = -1, /* malformed argument (message in rt_last_error) */
+  RT_ERR_UNSUPPORTED = -2, /* valid for the method but not supported here (e.g. order > 2) */
+  RT_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  RT_ERR_OOM = -4,         /* device or host allocation failed, or workspace too small */
+  RT_ERR_TIMEOUT = -5      /* a bounded device-side wait gave up */
+} rt_status;
+
+/* Per-trajectory outcome written to rt_outputs.status. */
+enum {
+  RT_TRAJ_TEND = 0,       /* the next event would fall after t_end (Table 2 loop condition) */
+  RT_TRAJ_MAX_EVENTS = 1, /* max_events events fired */
+  RT_TRAJ_ABSORBED = 2,   /* every propensity is zero: no event can ever fire */
+  RT_TRAJ_OVERFLOW = 3,   /* the next event would push a count above INT32_MAX (not fired) */
+  RT_TRAJ_TIMEOUT = 4,    /* a bounded cross-block wait gave up (large-network mode) */
+  RT_TRAJ_BAD_X0 = 5      /* a negative initial count */
+};
+
+/* Trajectory-to-hardware mappings. */
+enum {
+  RT_MAP_AUTO = -1,  /* chosen by the library from the network size */
+  RT_MAP_THREAD = 0, /* one thread per trajectory, state in registers (small M) */
+  RT_MAP_WARP = 1,   /* one warp per trajectory, channels spread over lanes */
+  RT_MAP_BLOCK = 2,  /* one thread block per trajectory, state in shared memory */
+  RT_MAP_BUNDLE = 3  /* several blocks per trajectory, state streamed through HBM */
+};
+
+typedef struct rt_network rt_network;
+typedef struct rt_batch rt_batch;
+
+/* Launch configuration; any field <= 0 (or mapping = RT_MAP_AUTO) means "choose". */
+typedef struct rt_launch_cfg {
+  int32_t mapping;       /* RT_MAP_* */
+  int32_t block_threads; /* threads per block */
+  int32_t ctas_per_traj; /* RT_MAP_BUNDLE: blocks cooperating on one trajectory */
+  int32_t reserved;
+} rt_launch_cfg;
+
+/* What to simulate. */
+typedef struct rt_run_params {
+  const int32_t *x0_dev;  /* initial counts: [N], or [n_traj][N] if per_traj_x0 */
+  int32_t per_traj_x0;
+  uint32_t stream_id;     /* 4th Philox counter word: independent streams per network */
+  double t_end;           /* simulate on [0, t_end]; +inf allowed when max_events bounds the run */
+  int64_t max_events;     /* per-trajectory event cap, 0 <= max_events <= INT32_MAX */
+  uint64_t seed;          /* Philox key */
+  int64_t n_traj;         /* number of trajectories, >= 0 */
+  int64_t traj_offset;    /* global id of trajectory 0 (Philox counter word 1 = lo32(offset + j)) */
+  double sample_dt;       /* grid spacing; <= 0: no grid.  Grid times are i*sample_dt, i < G */
+} rt_run_params;
+
+/* Where results go.  Any pointer may be NULL (output not produced). */
+typedef struct rt_outputs {
+  int32_t *x_final_dev;    /* [n_traj][N] state at the end of the run */
+  int32_t *grid_dev;       /* [n_traj][G][N] X at grid times (right-continuous); -1 = unknown */
+  int64_t *grid_sum_dev;   /* [G][N] += sum over trajectories of X(g) (wraps mod 2^64) */
+  int64_t *grid_sumsq_dev; /* [G][N] += sum over trajectories of X(g)^2 */
+  int64_t *grid_count_dev; /* [G]    += number of trajectories whose X(g) is known */
+  int64_t *n_events_dev;   /* [n_traj] events fired */
+  int32_t *status_dev;     /* [n_traj] RT_TRAJ_* */
+  double *t_last_dev;      /* [n_traj] time of the last fired event (0 if none) */
+  double *loglik_dev;      /* [n_traj] path log-likelihood sum ln a_mu - sum_k T_k(t_end) */
+  int32_t *counts_dev;     /* [n_traj][M] firings n_k per channel */
+  double *t_internal_dev;  /* [n_traj][M] internal times T_k(t_end) */
+} rt_outputs;
+
+/*
+ * rt_network_create -- validate and pack a network, copying it to the current device.
+ *
+ * Network in COO form as the paper stores it (Sec. 5, "Implementations"):
+ *   reactant coefficients sigma (reac_*: n_reac_nz entries, coef > 0) and net
+ *   state change v (stoi_*: n_stoi_nz entries), rates c[n_reactions] (Eq. 1).
+ * All arrays are host arrays, read during the call only.  Duplicate (reaction,
+ * species) entries are summed.  Requirements (else RT_ERR_INVALID_ARG):
+ * 1 <= n_species, 1 <= n_reactions, indices in range, c finite and >= 0, and a
+ * negative net change only on a reactant species with |v| <= sigma (counts can
+ * never go negative).  A reaction with more than two reactant molecules returns
+ * RT_ERR_UNSUPPORTED (the paper's two-reactant limit, Sec. 5).
+ * On success *out owns device memory until rt_network_destroy.
+ */
+int rt_network_create(int32_t n_species, int32_t n_reactions,
+                      int64_t n_reac_nz, const int32_t *reac_rxn, const int32_t *reac_sp,
+                      const int32_t *reac_coef,
+                      int64_t n_stoi_nz, const int32_t *stoi_rxn, const int32_t *stoi_sp,
+                      const int32_t *stoi_delta,
+                      const double *c, rt_network **out);
+
+/* Free a network (NULL is ignored).  The caller must ensure no work using it is in flight. */
+void rt_network_destroy(rt_network *net);
+
+/*
+ * rt_network_info -- sizes of a packed network.  Any output pointer may be NULL.
+ * max_dependents: the largest number of channels whose propensity one firing can
+ * change (the Gibson-Bruck dependency graph the paper mentions in Sec. 5).
+ */
+int rt_network_info(const rt_network *net, int32_t *n_species, int32_t *n_reactions,
+                    int32_t *max_dependents, int64_t *n_dependency_nz);
+
+/* Number of grid points on [0, t_end] for spacing sample_dt:
+ * floor(t_end / sample_dt * (1 + 1e-12)) + 1, or 0 if sample_dt <= 0 or t_end is not finite. */
+int64_t rt_grid_len(double t_end, double sample_dt);
+
+/*
+ * rt_workspace_bytes -- device scratch that rt_run needs for this network, run and
+ * launch configuration (0 for register/shared-memory mappings).  The caller
+ * allocates it (>= 256-byte aligned) and passes it to rt_run.
+ */
+int rt_workspace_bytes(const rt_network *net, const rt_run_params *params, const rt_launch_cfg *cfg,
+                       size_t *bytes);
+
+/*
+ * rt_run -- simulate params->n_traj independent trajectories of `net` (Table 2 of
+ * the paper in internal-time form: Eq. 24-27).
+ *
+ * Per trajectory j (global id g = traj_offset + j): X = X0, t = 0, T_k = 0,
+ * P_k = E(g,k,0), a_k = c_k h_k(X); then repeatedly: dt_k = (P_k - T_k)/a_k
+ * (+inf if a_k = 0, 0 if P_k <= T_k), mu = argmin (smallest k on ties); stop if
+ * no channel can fire, if t + dt_mu > t_end, if max_events fired, or if firing
+ * would overflow int32; else t += dt_mu, T_k += a_k dt_mu for all k, X += v_mu,
+ * P_mu += E(g, mu, n_mu), recompute a_k for the channels that depend on the
+ * changed species.  E(g,k,n) is the Philox4x32-10 Exp(1) draw described in
+ * rt_draw_exp1.  Grid samples use X after all events at times <= the grid time.
+ * With loglik/counts/t_internal outputs, T_k is advanced to t_end at the end
+ * (when the run reached t_end or was absorbed) and the log-likelihood
+ * sum_events ln a_mu - sum_k T_k (summed in k order) is written.
+ *
+ * x0 values are checked on the device (negative -> RT_TRAJ_BAD_X0).  workspace
+ * must be at least rt_workspace_bytes() (may be NULL when that is 0).
+ * grid_sum/sumsq/count are accumulated into (+=): zero them first.
+ */
+int rt_run(const rt_network *net, const rt_run_params *params, const rt_outputs *outputs,
+           const rt_launch_cfg *cfg, void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/*
+ * rt_loglik_backward -- gradient of sum_j grad_ll[j] * l_j with respect to the
+ * rate constants, from the counts and internal times saved by rt_run:
+ *   grad_c[k] = sum_j grad_ll[j] * (n_jk - T_jk(t_end)) / c_k
+ * (d l / d c_k = n_k / c_k - int h_k dt, since T_k = c_k int h_k dt; Eq. 16-18).
+ * grad_ll_dev [n_traj], counts_dev [n_traj][M], t_internal_dev [n_traj][M],
+ * grad_c_dev [M] (overwritten).  Entries with c_k = 0 come out as NaN.
+ */
+int rt_loglik_backward(const rt_network *net, int64_t n_traj, const double *grad_ll_dev,
+                       const int32_t *counts_dev, const double *t_internal_dev, double *grad_c_dev,
+                       void *stream);
+
+/*
+ * rt_draw_exp1 -- the Exp(1) internal-time increments of Eq. 24, E = ln(1/u), for
+ * count (traj, channel, index) triples (device arrays), as used by rt_run.
+ * Philox4x32-10 (Salmon et al., SC'11) with key (lo32(seed), hi32(seed)) and
+ * counter (index >> 1, lo32(traj), channel, stream_id); an even index takes
+ * output words (w0, w1), an odd one (w2, w3); v = (w1:w0) >> 12 and
+ * u = (2v + 1) 2^-53.  ln is a fixed-point evaluation (error <= 0.51 ulp)
+ * rounded once to binary64.  Writes u to u_dev and E to e_dev (either may be NULL).
+ */
+int rt_draw_exp1(uint64_t seed, uint32_t stream_id, int64_t count, const uint64_t *traj_dev,
+                 const uint32_t *channel_dev, const uint64_t *index_dev, double *u_dev, double *e_dev,
+                 void *stream);
+
+/* rt_log_eval -- the library's natural logarithm (used for ln a_mu) of count positive
+ * finite doubles x_dev, into y_dev. */
+int rt_log_eval(int64_t count, const double *x_dev, double *y_dev, void *stream);
+
+/* rt_philox -- raw Philox4x32-10 blocks: out_dev[4i..4i+3] = philox(ctr_dev[4i..], key). */
+int rt_philox(int64_t count, const uint32_t *ctr_dev, uint32_t key0, uint32_t key1, uint32_t *out_dev,
+              void *stream);
+
+/*
+ * Batched mode: many networks of uneven size in one persistent launch.
+ * rt_batch_create packs the networks (host handles, not consumed) into one
+ * device arena.  rt_batch_run simulates n_traj_per_net trajectories of every
+ * network; network i uses stream_id = i, so its results equal rt_run of that
+ * network with stream_id = i.  Per-network inputs (device arrays): x0 packed
+ * back to back in network order (sum of N_i entries), t_end [n_nets].
+ * Outputs packed the same way: x_final (sum_i n_traj*N_i), n_events and status
+ * (n_nets*n_traj), t_last (n_nets*n_traj).  Any output may be NULL.
+ */
+int rt_batch_create(int32_t n_nets, const rt_network *const *nets, rt_batch **out);
+void rt_batch_destroy(rt_batch *batch);
+int rt_batch_info(const rt_batch *batch, int64_t *total_species, int64_t *total_reactions);
+int rt_batch_run(rt_batch *batch, const int32_t *x0_dev, const double *t_end_dev, int64_t max_events,
+                 uint64_t seed, int64_t n_traj_per_net, int32_t *x_final_dev, int64_t *n_events_dev,
+                 int32_t *status_dev, double *t_last_dev, const rt_launch_cfg *cfg, void *stream);
+
+/* Message describing the last error on this host thread ("" if none). */
+const char *rt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RANDTIME_H */

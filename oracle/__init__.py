@@ -105,7 +105,7 @@ def grid_len(t_end: float, sample_dt: float, lib=None) -> int:
     return int((lib or load()).oracle_grid_len(float(t_end), float(sample_dt)))
 
 
-def run(net, x0, t_end, n_traj, seed=1, stream=0, traj_offset=0, max_events=(1 << 31) - 1,
+def run(net, x0, t_end, n_traj, seed=1, stream_id=0, traj_offset=0, max_events=(1 << 31) - 1,
         sample_dt=0.0, want_grid=False, want_grad=False, trace_len=0, n_threads=1, lib=None):
     """Run the oracle; returns a dict of numpy arrays.
 
@@ -134,7 +134,7 @@ def run(net, x0, t_end, n_traj, seed=1, stream=0, traj_offset=0, max_events=(1 <
         out["trace_t"] = np.zeros((n_traj, trace_len), np.float64)
     rc = lib.oracle_run(N, M, len(net.reac_rxn), _p(net.reac_rxn), _p(net.reac_sp), _p(net.reac_coef),
                         len(net.stoi_rxn), _p(net.stoi_rxn), _p(net.stoi_sp), _p(net.stoi_delta),
-                        _p(net.c), _p(x0), per, float(t_end), int(max_events), int(seed), int(stream),
+                        _p(net.c), _p(x0), per, float(t_end), int(max_events), int(seed), int(stream_id),
                         n_traj, int(traj_offset), float(sample_dt),
                         _p(out["x_final"]), _p(out.get("grid")), _p(out["n_events"]), _p(out["status"]),
                         _p(out["t_last"]), _p(out.get("loglik")), _p(out.get("counts")),

@@ -1,0 +1,205 @@
+"""High-level Python API over librandtime (PyTorch for device memory and streams).
+
+Everything that simulates runs in the library's CUDA kernels; this module only
+allocates torch tensors, fills the C structs and calls the C ABI.
+
+  Network(net)                    -- a packed network on the current CUDA device
+  simulate(...)                   -- run trajectories (Table 2 of the paper), torch outputs
+  LogLik.apply(c, ...)            -- path log-likelihood with a backward kernel for d/dc
+  draw_exp1 / log_eval / philox   -- the library's random draws and logarithm
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from .workloads import Network as NetworkSpec
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device=None):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class Network:
+    """A network packed and copied to the current CUDA device (rt_network_create)."""
+
+    def __init__(self, spec: NetworkSpec, c=None):
+        self.lib = L.load()
+        self.spec = spec if c is None else spec.with_rates(np.asarray(c, dtype=np.float64))
+        s = self.spec
+        h = ctypes.c_void_p()
+        arrs = [s.reac_rxn, s.reac_sp, s.reac_coef, s.stoi_rxn, s.stoi_sp, s.stoi_delta]
+        p = [a.ctypes.data_as(ctypes.c_void_p) for a in arrs]
+        L.check(self.lib.rt_network_create(s.n_species, s.n_reactions, len(s.reac_rxn), p[0], p[1], p[2],
+                                           len(s.stoi_rxn), p[3], p[4], p[5],
+                                           s.c.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)),
+                "rt_network_create")
+        self.handle = h
+        self.N, self.M = s.n_species, s.n_reactions
+        self.device = torch.cuda.current_device()
+
+    def info(self):
+        n, m, md = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        nz = ctypes.c_int64()
+        L.check(self.lib.rt_network_info(self.handle, ctypes.byref(n), ctypes.byref(m), ctypes.byref(md),
+                                         ctypes.byref(nz)), "rt_network_info")
+        return dict(n_species=n.value, n_reactions=m.value, max_dependents=md.value, n_dependency_nz=nz.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.rt_network_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def launch_cfg(mapping: Optional[int] = None, block_threads: int = 0, ctas_per_traj: int = 0):
+    return L.rt_launch_cfg(L.RT_MAP_AUTO if mapping is None else int(mapping), int(block_threads),
+                           int(ctas_per_traj), 0)
+
+
+def grid_len(t_end: float, sample_dt: float) -> int:
+    return int(L.load().rt_grid_len(float(t_end), float(sample_dt)))
+
+
+def simulate(net: Network, x0, t_end: float, n_traj: int, seed: int = 1, stream_id: int = 0,
+             traj_offset: int = 0, max_events: int = (1 << 31) - 1, sample_dt: float = 0.0,
+             grid: str = "none", grad: bool = False, mapping: Optional[int] = None, block_threads: int = 0,
+             ctas_per_traj: int = 0, outputs: Optional[dict] = None) -> dict:
+    """Simulate n_traj trajectories; returns a dict of CUDA tensors.
+
+    x0: [N] or [n_traj, N] int32 (numpy, list or tensor; copied to the device if needed).
+    grid: "none", "traj" (per-trajectory [n_traj, G, N]) or "moments" (sums over
+    trajectories of X and X^2 per grid point, plus counts).
+    grad: also return loglik [n_traj], counts [n_traj, M], t_internal [n_traj, M].
+    outputs: optional preallocated tensors (same keys) to write into.
+    """
+    lib = L.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    N, M = net.N, net.M
+    x0t = torch.as_tensor(x0, dtype=torch.int32)
+    if x0t.device != dev:
+        x0t = x0t.to(dev)
+    x0t = x0t.contiguous()
+    per = 1 if x0t.dim() == 2 else 0
+    if per and x0t.shape[0] != n_traj:
+        raise ValueError("per-trajectory x0 must have n_traj rows")
+    G = grid_len(t_end, sample_dt) if grid != "none" else 0
+    out = dict(outputs or {})
+
+    def get(name, shape, dtype, zero=False):
+        if name not in out:
+            out[name] = (torch.zeros if zero else torch.empty)(shape, dtype=dtype, device=dev)
+        return out[name]
+
+    o = L.rt_outputs()
+    o.x_final_dev = _ptr(get("x_final", (n_traj, N), torch.int32))
+    o.n_events_dev = _ptr(get("n_events", (n_traj,), torch.int64))
+    o.status_dev = _ptr(get("status", (n_traj,), torch.int32))
+    o.t_last_dev = _ptr(get("t_last", (n_traj,), torch.float64))
+    if grid == "traj":
+        o.grid_dev = _ptr(get("grid", (n_traj, G, N), torch.int32))
+    elif grid == "moments":
+        o.grid_sum_dev = _ptr(get("grid_sum", (G, N), torch.int64, True))
+        o.grid_sumsq_dev = _ptr(get("grid_sumsq", (G, N), torch.int64, True))
+        o.grid_count_dev = _ptr(get("grid_count", (G,), torch.int64, True))
+    elif grid != "none":
+        raise ValueError("grid must be 'none', 'traj' or 'moments'")
+    if grad:
+        o.loglik_dev = _ptr(get("loglik", (n_traj,), torch.float64))
+        o.counts_dev = _ptr(get("counts", (n_traj, M), torch.int32))
+        o.t_internal_dev = _ptr(get("t_internal", (n_traj, M), torch.float64))
+
+    p = L.rt_run_params(_ptr(x0t), per, int(stream_id), float(t_end), int(max_events), int(seed) & (2**64 - 1),
+                        int(n_traj), int(traj_offset), float(sample_dt))
+    cfg = launch_cfg(mapping, block_threads, ctas_per_traj)
+    nbytes = ctypes.c_size_t(0)
+    L.check(lib.rt_workspace_bytes(net.handle, ctypes.byref(p), ctypes.byref(cfg), ctypes.byref(nbytes)),
+            "rt_workspace_bytes")
+    ws = out.get("_workspace")
+    if nbytes.value and (ws is None or ws.numel() < nbytes.value):
+        ws = torch.empty(nbytes.value, dtype=torch.uint8, device=dev)
+    if not nbytes.value:
+        ws = None
+    L.check(lib.rt_run(net.handle, ctypes.byref(p), ctypes.byref(o), ctypes.byref(cfg), _ptr(ws), nbytes.value,
+                       _stream()), "rt_run")
+    out["_x0"] = x0t  # keep inputs alive until the stream has consumed them
+    if ws is not None:
+        out["_workspace"] = ws
+    return out
+
+
+def loglik_backward(net: Network, grad_ll: torch.Tensor, counts: torch.Tensor, t_internal: torch.Tensor):
+    lib = L.load()
+    grad_c = torch.empty(net.M, dtype=torch.float64, device=counts.device)
+    L.check(lib.rt_loglik_backward(net.handle, counts.shape[0], _ptr(grad_ll.contiguous()), _ptr(counts),
+                                   _ptr(t_internal), _ptr(grad_c), _stream()), "rt_loglik_backward")
+    return grad_c
+
+
+class LogLik(torch.autograd.Function):
+    """Trajectory log-likelihoods l_j(c) = sum ln a_mu - sum_k T_k(t_end) (Eq. 16-18), with
+    d l_j / d c_k = (n_jk - T_jk(t_end)) / c_k computed by the backward kernel.
+
+    forward(c [M] float64, spec, x0, t_end, n_traj, seed, stream_id, max_events) -> l [n_traj]
+    """
+
+    @staticmethod
+    def forward(ctx, c, spec, x0, t_end, n_traj, seed=1, stream_id=0, max_events=(1 << 31) - 1):
+        net = Network(spec, c.detach().cpu().numpy())
+        out = simulate(net, x0, t_end, n_traj, seed=seed, stream_id=stream_id, max_events=max_events, grad=True)
+        ctx.net = net
+        ctx.c_device = c.device
+        ctx.save_for_backward(out["counts"], out["t_internal"])
+        ctx.out = out
+        return out["loglik"]
+
+    @staticmethod
+    def backward(ctx, grad_ll):
+        counts, t_internal = ctx.saved_tensors
+        g = loglik_backward(ctx.net, grad_ll.to(device=counts.device, dtype=torch.float64), counts, t_internal)
+        return g.to(ctx.c_device), None, None, None, None, None, None, None
+
+
+def draw_exp1(seed: int, traj, channel, index, stream_id: int = 0):
+    """(u, E) of the library's Philox Exp(1) draws for the given (traj, channel, index) triples."""
+    lib = L.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tr = torch.as_tensor(np.asarray(traj, dtype=np.uint64).view(np.int64)).to(dev)
+    ch = torch.as_tensor(np.asarray(channel, dtype=np.uint32).view(np.int32)).to(dev)
+    ix = torch.as_tensor(np.asarray(index, dtype=np.uint64).view(np.int64)).to(dev)
+    n = tr.numel()
+    u = torch.empty(n, dtype=torch.float64, device=dev)
+    e = torch.empty(n, dtype=torch.float64, device=dev)
+    L.check(lib.rt_draw_exp1(int(seed), int(stream_id), n, _ptr(tr), _ptr(ch), _ptr(ix), _ptr(u), _ptr(e),
+                             _stream()), "rt_draw_exp1")
+    return u, e
+
+
+def log_eval(x: torch.Tensor) -> torch.Tensor:
+    lib = L.load()
+    x = x.to(torch.float64).contiguous()
+    y = torch.empty_like(x)
+    L.check(lib.rt_log_eval(x.numel(), _ptr(x), _ptr(y), _stream()), "rt_log_eval")
+    return y
+
+
+def philox(ctr: torch.Tensor, key0: int, key1: int) -> torch.Tensor:
+    lib = L.load()
+    c = ctr.contiguous()
+    out = torch.empty_like(c)
+    L.check(lib.rt_philox(c.numel() // 4, _ptr(c), int(key0), int(key1), _ptr(out), _stream()), "rt_philox")
+    return out

@@ -1,0 +1,42 @@
+// rt_filter.cuh -- cheap, rigorous bounds that let the argmin skip exact divisions.
+//
+// The waiting time of Eq. 25 is w = fl((P - T) / a).  Computing it costs a
+// binary64 subtraction and division, which on GB300 occupy the FP64 pipe for
+// about nine issue slots.  Most channels cannot be the minimum, and that can be
+// shown with single-precision arithmetic: truncating the high 32-bit word of a
+// non-negative double to a float (integer ops only, no FP64 conversion) gives a
+// lower bound; adding one unit in the 20th mantissa bit gives an upper bound;
+// float operations with directed rounding then give a certified lower bound of
+// (P - T) and an upper bound of t * a.  A channel is skipped only if
+//   (P - T)_lower > (t * a)_upper,  i.e.  its exact quotient exceeds t,
+// so the exact minimum (with smallest-index ties) is unchanged.
+#pragma once
+#include <cstdint>
+
+namespace rt {
+
+// largest float <= x for a double x >= 0 (0 below FLT_MIN, FLT_MAX above it)
+__device__ __forceinline__ float f32_lower(double x) {
+  const uint32_t hi = (uint32_t)((uint64_t)__double_as_longlong(x) >> 32);
+  const int e = (int)(hi >> 20) - 1023 + 127;
+  if (e <= 0) return 0.0f;
+  if (e >= 255) return 3.4028234663852886e38f;
+  return __uint_as_float(((uint32_t)e << 23) | ((hi & 0xFFFFFu) << 3));
+}
+
+// a float >= x for a double x >= 0 (FLT_MIN below it, +inf above FLT_MAX)
+__device__ __forceinline__ float f32_upper(double x) {
+  const uint32_t hi = (uint32_t)((uint64_t)__double_as_longlong(x) >> 32);
+  const int e = (int)(hi >> 20) - 1023 + 127;
+  if (e <= 0) return 1.17549435e-38f;
+  if (e >= 255) return __int_as_float(0x7F800000);
+  return __uint_as_float((((uint32_t)e << 23) | ((hi & 0xFFFFFu) << 3)) + 8u);  // + one 2^-20 unit
+}
+
+// True if the exact (P - T) / a is certainly > thr (a > 0, T >= 0, thr >= 0).
+__device__ __forceinline__ bool exceeds(double P, double T, double a, float thr) {
+  const float rem_lo = __fsub_rd(f32_lower(P), f32_upper(T));
+  return rem_lo > __fmul_ru(thr, f32_upper(a));
+}
+
+}  // namespace rt

@@ -1,0 +1,78 @@
+// rt_internal.h -- shared declarations of librandtime's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "randtime.h"
+
+namespace rt {
+
+// Reactant descriptor of one reaction (at most two reactant molecules, as in the
+// paper's Sec. 5): h = 1 (s0 < 0), x[s0] (s1 == -1), x[s0](x[s0]-1)/2 (s1 == -2),
+// or x[s0] * x[s1] (s1 >= 0).
+enum : int32_t { RD_NONE = -1, RD_UNI = -1, RD_DIMER = -2 };
+
+// Device view of a packed network.
+struct DevNet {
+  int32_t N, M;
+  int32_t n_vnz;           // entries in vlist
+  int32_t max_vlen;        // largest number of species one reaction changes
+  const int2 *rdesc;       // [M] {s0, s1}
+  const double *c;         // [M]
+  const int32_t *vptr;     // [M+1] net change of reaction k: vlist[vptr[k]..vptr[k+1])
+  const int2 *vlist;       // {species, delta}
+  const int32_t *sptr;     // [N+1] reactions with species s as a reactant: slist[sptr[s]..sptr[s+1])
+  const int32_t *slist;
+  const uint64_t *depmask; // [M] (M <= 64 only) bit k: firing changes a species channel k reads
+  const uint8_t *depw;     // [M][32] (M <= 256 only) bit r of depw[mu*32 + l]: channel l + 32 r depends on mu
+};
+
+}  // namespace rt
+
+struct rt_network {
+  rt::DevNet dev;
+  void *arena = nullptr;   // device allocation holding every array of dev
+  size_t arena_bytes = 0;
+  int device = 0;
+  int32_t max_dependents = 0;  // upper bound, counted with multiplicity
+  int64_t n_dep_nz = 0;
+  // host copies used by the batched mode's packer
+  std::string host_blob;  // the arena's bytes
+  size_t off_rdesc = 0, off_c = 0, off_vptr = 0, off_vlist = 0, off_sptr = 0, off_slist = 0, off_dep = 0;
+  size_t off_depw = 0;
+};
+
+namespace rt {
+
+// Thread-local error message; returns `code`.
+int set_error(int code, const char *fmt, ...);
+void clear_error();
+
+// Arguments of a simulation launch (plain data, passed by value to kernels).
+struct RunArgs {
+  DevNet net;
+  const int32_t *x0;
+  int32_t per_traj_x0;
+  uint32_t stream_id;
+  double t_end;
+  int32_t max_events;
+  uint64_t seed;
+  int64_t n_traj;
+  int64_t traj_offset;
+  double sample_dt;
+  int64_t G;
+  rt_outputs out;
+};
+
+// Launchers implemented in the .cu files (return RT_OK or an error code).
+int launch_thread_mapping(const RunArgs &a, int block_threads, cudaStream_t s);
+int thread_mapping_max_m();
+size_t bundle_workspace_bytes(const DevNet &net, int64_t n_traj, int ctas_per_traj);
+int launch_warp_mapping(const RunArgs &a, int block_threads, cudaStream_t s);
+int warp_mapping_max_m();
+int launch_block_mapping(const RunArgs &a, int block_threads, cudaStream_t s);
+int block_mapping_max_m();
+int launch_bundle_mapping(const RunArgs &a, int ctas_per_traj, void *ws, size_t ws_bytes, cudaStream_t s);
+
+}  // namespace rt

@@ -1,0 +1,88 @@
+// rt_sim.cuh -- per-event building blocks shared by the simulation kernels.
+//
+// Floating-point rules (so every mapping reproduces the same bits): each
+// operation is one explicitly rounded binary64 op (__dadd_rn, __dsub_rn,
+// __dmul_rn, __ddiv_rn; never contracted into an FMA).  Comparisons of values
+// known to be non-negative (times, waiting times, propensities) are done on
+// their bit patterns as signed 64-bit integers, which orders them exactly like
+// the doubles and keeps the comparison off GB300's narrow FP64 pipe.
+#pragma once
+#include <cstdint>
+
+#include "rt_filter.cuh"
+#include "rt_internal.h"
+#include "rt_rng.cuh"
+
+namespace rt {
+
+__device__ __forceinline__ int64_t dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ double bitsd(int64_t b) { return __longlong_as_double(b); }
+constexpr int64_t kInfBits = 0x7FF0000000000000ll;
+
+// Exact binary64 value of 0 <= h < 2^53 built with integer instructions (the
+// hardware int64 -> double conversion issues on the FP64 pipe); larger h rounds
+// through the hardware conversion.
+__device__ __forceinline__ double i64_to_f64(int64_t h) {
+  if (h <= 0) return h == 0 ? 0.0 : __ll2double_rn(h);
+  if (h >= (1ll << 53)) return __ll2double_rn(h);
+  const int e = 63 - __clzll(h);  // position of the leading one, <= 52
+  const uint64_t mant = (uint64_t)h << (52 - e);
+  return __longlong_as_double((long long)((((uint64_t)(e + 1023)) << 52) | (mant & 0x000FFFFFFFFFFFFFull)));
+}
+
+// h_k(X) of Eq. 2 for a descriptor {s0, s1}, exact in int64, then a_k = c_k h_k (Eq. 1).
+template <typename XAt>
+__device__ __forceinline__ double propensity(int2 rd, double c, XAt x) {
+  int64_t h;
+  if (rd.x < 0) {
+    h = 1;
+  } else {
+    const int64_t x0 = x(rd.x);
+    if (rd.y == RD_UNI) h = x0;
+    else if (rd.y == RD_DIMER) h = x0 * (x0 - 1) / 2;
+    else h = x0 * (int64_t)x(rd.y);
+  }
+  return __dmul_rn(c, i64_to_f64(h));
+}
+
+// Waiting time (P - T) / a of Eq. 25 for a > 0: 0 if no internal time is left.
+__device__ __forceinline__ double waiting_time(double P, double T, double a) {
+  const double rem = __dsub_rn(P, T);
+  return dbits(rem) > 0 ? __ddiv_rn(rem, a) : 0.0;
+}
+
+// The same from an already computed remainder rem = fl(P - T).
+__device__ __forceinline__ double waiting_time_rem(double rem, double a) {
+  return dbits(rem) > 0 ? __ddiv_rn(rem, a) : 0.0;
+}
+
+// A float upper bound of the exact quotient rem / a (rem > 0, a > 0).
+__device__ __forceinline__ float quot_upper(double rem, double a) {
+  const float al = f32_lower(a);
+  return al > 0.0f ? __fdiv_ru(f32_upper(rem), al) : __int_as_float(0x7F800000);
+}
+
+// True if the exact quotient rem / a is certainly > thr (rem > 0, a > 0).
+__device__ __forceinline__ bool quot_exceeds(double rem, double a, float thr) {
+  return f32_lower(rem) > __fmul_ru(thr, f32_upper(a));
+}
+
+// float upper bound of (P - T) / a (0 if P - T may be <= 0)
+__device__ __forceinline__ float wait_upper(double P, double T, double a) {
+  const float rem = __fsub_ru(f32_upper(P), f32_lower(T));
+  if (!(rem > 0.0f)) return 0.0f;
+  const float al = f32_lower(a);
+  return al > 0.0f ? __fdiv_ru(rem, al) : __int_as_float(0x7F800000);
+}
+
+// Register-array element r (runtime) by predicated selects, so arrays indexed with
+// compile-time indices stay in registers.
+template <int R, typename T>
+__device__ __forceinline__ T pick(const T (&v)[R], int r) {
+  T out = v[0];
+#pragma unroll
+  for (int i = 1; i < R; ++i) out = (i == r) ? v[i] : out;
+  return out;
+}
+
+}  // namespace rt

@@ -1,0 +1,317 @@
+// rt_traj_block.cuh -- one thread block per trajectory, state in registers.
+//
+// The NRRTA loop of Table 2 (Liu & Wang, arXiv:2103.00405) for networks of up to
+// 8 * blockDim.x reactions: channel k lives in thread k % B, register slot k / B
+// (P_k, T_k, a_k, n_k; Eq. 17-27), X in shared memory.  Per event:
+//   1. the channels that read a species the last firing changed are marked in a
+//      shared bitmap from the species -> reactions lists (dependency graph, Sec. 5);
+//   2. each thread fires its own bookkeeping (new Exp(1) draw, Eq. 27), advances
+//      its internal times with the pre-event propensities (Eq. 17), recomputes the
+//      marked propensities (Eq. 1-2) and proposes its smallest certified upper
+//      bound of the waiting time;
+//   3. the block's best candidate is computed exactly and broadcast, every thread
+//      computes exactly only channels not certified to be larger, and a block
+//      reduction on (waiting time bits, channel) gives the exact argmin (Eq. 25-26).
+#pragma once
+#include <climits>
+
+#include "rt_sim.cuh"
+
+namespace rt {
+
+struct BlockNet {
+  int M, N;
+  const int2 *rd;
+  const double *c;
+  const int *vp;
+  const int2 *vl;
+  const int *sptr;
+  const int *slist;
+};
+
+// shared-memory scratch of one block trajectory
+struct BlockScratch {
+  int *X;           // [N]
+  uint32_t *bm;     // [ceil(M/32)]
+  float *red_u;     // [warps]
+  int *red_k;       // [warps]
+  long long *red_w; // [warps]
+  int *red_k2;      // [warps]
+  double *buf;      // [B] (and the broadcast slots below)
+  long long *s_wc;  // candidate's exact waiting time
+  double *s_amu;    // propensity of the fired channel
+};
+
+__host__ __device__ inline size_t block_scratch_bytes(int M, int N, int B) {
+  const int W = B / 32;
+  return (size_t)N * 4 + (size_t)((M + 31) / 32) * 4 + (size_t)W * (4 + 4 + 8 + 4) + (size_t)B * 8 + 16 + 64;
+}
+
+__device__ inline BlockScratch carve_block_scratch(unsigned char *base, int M, int N, int B) {
+  const int W = B / 32;
+  BlockScratch s;
+  s.buf = (double *)base;
+  s.red_w = (long long *)(s.buf + B);
+  s.s_wc = s.red_w + W;
+  s.s_amu = (double *)(s.s_wc + 1);
+  s.red_u = (float *)(s.s_amu + 1);
+  s.red_k = (int *)(s.red_u + W);
+  s.red_k2 = s.red_k + W;
+  s.bm = (uint32_t *)(s.red_k2 + W);
+  s.X = (int *)(s.bm + (M + 31) / 32);
+  return s;
+}
+
+template <int R, bool LL>
+__device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNet &net, const BlockScratch &S, const int64_t j,
+                                 const int tend_finite) {
+  const int tid = threadIdx.x, B = blockDim.x, lane = tid & 31, warp = tid >> 5, W = B >> 5;
+  const int M = net.M, N = net.N;
+  const int nbm = (M + 31) / 32;
+  const uint64_t g = (uint64_t)(A.traj_offset + j);
+  const int32_t *x0 = A.x0 + (A.per_traj_x0 ? j * (int64_t)N : 0);
+  int *X = S.X;
+  for (int s = tid; s < N; s += B) X[s] = x0[s];
+  for (int w = tid; w < nbm; w += B) S.bm[w] = 0u;
+  __syncthreads();
+  int badl = 0;
+  for (int s = tid; s < N; s += B) badl |= X[s] < 0;
+  const bool bad = __syncthreads_or(badl) != 0;
+  auto xat = [&](int s) { return X[s]; };
+
+  auto record = [&](int64_t gidx, bool known) {
+    if (A.out.grid_dev) {
+      int32_t *gp = A.out.grid_dev + (j * A.G + gidx) * N;
+      for (int s = tid; s < N; s += B) gp[s] = known ? X[s] : -1;
+    }
+    if (!known || !A.out.grid_sum_dev) return;
+    for (int s = tid; s < N; s += B) {
+      const long long x = X[s];
+      atomicAdd((unsigned long long *)(A.out.grid_sum_dev + gidx * N + s), (unsigned long long)x);
+      if (A.out.grid_sumsq_dev)
+        atomicAdd((unsigned long long *)(A.out.grid_sumsq_dev + gidx * N + s), (unsigned long long)(x * x));
+    }
+    if (tid == 0 && A.out.grid_count_dev) atomicAdd((unsigned long long *)(A.out.grid_count_dev + gidx), 1ull);
+  };
+
+  auto mark = [&](int mu, bool set) {
+    for (int i = net.vp[mu]; i < net.vp[mu + 1]; ++i) {
+      const int s = net.vl[i].x;
+      for (int q = net.sptr[s] + tid; q < net.sptr[s + 1]; q += B) {
+        const int ch = net.slist[q];
+        if (set) atomicOr(&S.bm[ch >> 5], 1u << (ch & 31));
+        else S.bm[ch >> 5] = 0u;
+      }
+    }
+  };
+
+  double P[R], T[R], a[R];
+  int32_t n[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int k = tid + B * r;
+    P[r] = 0.0;
+    T[r] = 0.0;
+    a[r] = 0.0;
+    n[r] = 0;
+    if (!bad && k < M) {
+      P[r] = exp1_draw(A.seed, g, (uint32_t)k, 0u, A.stream_id);
+      a[r] = propensity(net.rd[k], net.c[k], xat);
+    }
+  }
+  int status = bad ? RT_TRAJ_BAD_X0 : RT_TRAJ_TEND;
+  double t = 0.0, ll = 0.0, dprev = 0.0;
+  int mu_prev = -1;
+  int32_t ev = 0;
+  int64_t gi = 0;
+  double next_g = 0.0;
+  const int64_t tend_bits = dbits(A.t_end);
+
+  if (!bad) {
+    for (;;) {
+      if (mu_prev >= 0) mark(mu_prev, true);
+      __syncthreads();
+      const bool adv = dbits(dprev) != 0;
+      float ub = __int_as_float(0x7F800000);
+      int kub = INT_MAX;
+      if (mu_prev >= 0 && tid == mu_prev % B) {  // Eq. 27: the fired channel draws its next increment
+        const int rm = mu_prev / B;
+        const int32_t nm = pick<R>(n, rm) + 1;
+        const double E = exp1_draw(A.seed, g, (uint32_t)mu_prev, (uint32_t)nm, A.stream_id);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (r == rm) {
+            n[r] = nm;
+            P[r] = __dadd_rn(P[r], E);
+          }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int k = tid + B * r;
+        if (k < M) {
+          if (adv && dbits(a[r]) != 0) T[r] = __dadd_rn(T[r], __dmul_rn(a[r], dprev));
+          if ((S.bm[k >> 5] >> (k & 31)) & 1u) a[r] = propensity(net.rd[k], net.c[k], xat);
+          if (dbits(a[r]) != 0) {
+            const float u = wait_upper(P[r], T[r], a[r]);
+            if (kub == INT_MAX || u < ub) {
+              ub = u;
+              kub = k;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float u2 = __shfl_xor_sync(0xFFFFFFFFu, ub, o);
+        const int k2 = __shfl_xor_sync(0xFFFFFFFFu, kub, o);
+        if (u2 < ub || (u2 == ub && k2 < kub)) {
+          ub = u2;
+          kub = k2;
+        }
+      }
+      if (lane == 0) {
+        S.red_u[warp] = ub;
+        S.red_k[warp] = kub;
+      }
+      __syncthreads();
+      ub = S.red_u[0];
+      kub = S.red_k[0];
+      for (int w = 1; w < W; ++w) {
+        const float u2 = S.red_u[w];
+        const int k2 = S.red_k[w];
+        if (u2 < ub || (u2 == ub && k2 < kub)) {
+          ub = u2;
+          kub = k2;
+        }
+      }
+      if (kub == INT_MAX) {
+        status = RT_TRAJ_ABSORBED;
+        break;
+      }
+      if (tid == (kub % B)) {
+        const int rs = kub / B;
+        *S.s_wc = dbits(waiting_time(pick<R>(P, rs), pick<R>(T, rs), pick<R>(a, rs)));
+      }
+      __syncthreads();
+      const long long wc = *S.s_wc;
+      const float thr = f32_upper(bitsd(wc));
+      long long bw = wc;
+      int bk = kub;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int k = tid + B * r;
+        if (k < M && k != kub && dbits(a[r]) != 0 && !exceeds(P[r], T[r], a[r], thr)) {
+          const long long wb = dbits(waiting_time(P[r], T[r], a[r]));
+          if (wb < bw || (wb == bw && k < bk)) {
+            bw = wb;
+            bk = k;
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long w2 = __shfl_xor_sync(0xFFFFFFFFu, bw, o);
+        const int k2 = __shfl_xor_sync(0xFFFFFFFFu, bk, o);
+        if (w2 < bw || (w2 == bw && k2 < bk)) {
+          bw = w2;
+          bk = k2;
+        }
+      }
+      if (lane == 0) {
+        S.red_w[warp] = bw;
+        S.red_k2[warp] = bk;
+      }
+      __syncthreads();
+      bw = S.red_w[0];
+      bk = S.red_k2[0];
+      for (int w = 1; w < W; ++w) {
+        const long long w2 = S.red_w[w];
+        const int k2 = S.red_k2[w];
+        if (w2 < bw || (w2 == bw && k2 < bk)) {
+          bw = w2;
+          bk = k2;
+        }
+      }
+      const int mu = bk;
+      if (LL && tid == (mu % B)) *S.s_amu = pick<R>(a, mu / B);
+      if (mu_prev >= 0) mark(mu_prev, false);  // bits were read before the last barrier
+      const double dmin = bitsd(bw);
+      const double tn = __dadd_rn(t, dmin);
+      if (dbits(tn) > tend_bits) {
+        status = RT_TRAJ_TEND;
+        break;
+      }
+      if (ev == A.max_events) {
+        status = RT_TRAJ_MAX_EVENTS;
+        break;
+      }
+      bool over = false;
+      for (int i = net.vp[mu]; i < net.vp[mu + 1]; ++i) {
+        const int2 e = net.vl[i];
+        const long long nx = (long long)X[e.x] + e.y;
+        over |= (nx > INT_MAX) | (nx < 0);
+      }
+      if (over) {
+        status = RT_TRAJ_OVERFLOW;
+        break;
+      }
+      while (gi < A.G && dbits(next_g) < dbits(tn)) {
+        record(gi, true);
+        ++gi;
+        next_g = __dmul_rn(__ll2double_rn(gi), A.sample_dt);
+      }
+      t = tn;
+      __syncthreads();  // all reads of X and of the amu slot for this event are done
+      if (LL && tid == 0) ll = __dadd_rn(ll, rt_ln(*S.s_amu));
+      for (int i = net.vp[mu] + tid; i < net.vp[mu + 1]; i += B) {
+        const int2 e = net.vl[i];
+        X[e.x] += e.y;
+      }
+      ++ev;
+      dprev = dmin;
+      mu_prev = mu;
+    }
+  }
+
+  __syncthreads();
+  const bool known = status == RT_TRAJ_TEND || status == RT_TRAJ_ABSORBED;
+  for (; gi < A.G; ++gi) record(gi, known);
+  if (A.out.loglik_dev || A.out.t_internal_dev) {
+    if (known && tend_finite && !bad) {
+      const double rest = __dsub_rn(A.t_end, t);
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (tid + B * r < M) T[r] = __dadd_rn(T[r], __dmul_rn(a[r], rest));
+    }
+    if (A.out.t_internal_dev)
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (tid + B * r < M) A.out.t_internal_dev[j * M + tid + B * r] = T[r];
+    if (A.out.loglik_dev) {
+      double sT = 0.0;  // sum_k T_k in k order, B values at a time through shared memory
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        S.buf[tid] = T[r];
+        __syncthreads();
+        if (tid == 0)
+          for (int l = 0; l < B && l + B * r < M; ++l) sT = __dadd_rn(sT, S.buf[l]);
+        __syncthreads();
+      }
+      if (tid == 0) A.out.loglik_dev[j] = bad ? __longlong_as_double(0x7FF8000000000000ll) : __dsub_rn(ll, sT);
+    }
+  }
+  if (A.out.counts_dev)
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (tid + B * r < M) A.out.counts_dev[j * M + tid + B * r] = n[r];
+  if (A.out.x_final_dev)
+    for (int s = tid; s < N; s += B) A.out.x_final_dev[j * N + s] = X[s];
+  if (tid == 0) {
+    if (A.out.n_events_dev) A.out.n_events_dev[j] = ev;
+    if (A.out.status_dev) A.out.status_dev[j] = status;
+    if (A.out.t_last_dev) A.out.t_last_dev[j] = t;
+  }
+  __syncthreads();
+}
+
+}  // namespace rt

@@ -201,13 +201,23 @@ def lv_config(n_traj: int = 64):
                 sample_dt=0.01, n_traj=n_traj, seed=1)
 
 
+# Per-trajectory event cap of the ensemble workload.  A Lotka-Volterra trajectory
+# whose predators die out lets the prey grow until int32 overflow (~2^31 events in
+# one thread); typical trajectories to t = 10 fire ~3.1e5 events.  Capped
+# trajectories end with status MAX_EVENTS and are reported, not dropped.
+ENSEMBLE_MAX_EVENTS = 4_000_000
+
+
 def ensemble_configs(n_traj: int = 1 << 20):
     """Lotka-Volterra, birth-death (k=100, gamma=1, A0=0) and dimerisation (0.001/0.1, A0=1000, B0=0),
     each n_traj trajectories to t_end = 10."""
+    cap = ENSEMBLE_MAX_EVENTS
     return [
-        dict(net=lotka_volterra(), x0=np.array([1000, 1000], np.int32), t_end=10.0, n_traj=n_traj, seed=1),
-        dict(net=birth_death(), x0=np.array([0], np.int32), t_end=10.0, n_traj=n_traj, seed=1),
-        dict(net=dimerisation(), x0=np.array([1000, 0], np.int32), t_end=10.0, n_traj=n_traj, seed=1),
+        dict(net=lotka_volterra(), x0=np.array([1000, 1000], np.int32), t_end=10.0, n_traj=n_traj, seed=1,
+             max_events=cap),
+        dict(net=birth_death(), x0=np.array([0], np.int32), t_end=10.0, n_traj=n_traj, seed=1, max_events=cap),
+        dict(net=dimerisation(), x0=np.array([1000, 0], np.int32), t_end=10.0, n_traj=n_traj, seed=1,
+             max_events=cap),
     ]
 
 
