@@ -62,7 +62,7 @@ enum {
   RT_MAP_AUTO = -1,  /* chosen by the library from the network size */
   RT_MAP_THREAD = 0, /* one thread per trajectory, state in registers (small M) */
   RT_MAP_WARP = 1,   /* one warp per trajectory, channels spread over lanes */
-  RT_MAP_BLOCK = 2,  /* one thread block per trajectory, state in shared memory */
+  RT_MAP_BLOCK = 2,  /* one thread block per trajectory, state in registers (M <= 8 * block_threads) */
   RT_MAP_BUNDLE = 3  /* several blocks per trajectory, state streamed through HBM */
 };
 
@@ -207,20 +207,49 @@ int rt_philox(int64_t count, const uint32_t *ctr_dev, uint32_t key0, uint32_t ke
 
 /*
  * Batched mode: many networks of uneven size in one persistent launch.
- * rt_batch_create packs the networks (host handles, not consumed) into one
- * device arena.  rt_batch_run simulates n_traj_per_net trajectories of every
- * network; network i uses stream_id = i, so its results equal rt_run of that
- * network with stream_id = i.  Per-network inputs (device arrays): x0 packed
- * back to back in network order (sum of N_i entries), t_end [n_nets].
- * Outputs packed the same way: x_final (sum_i n_traj*N_i), n_events and status
- * (n_nets*n_traj), t_last (n_nets*n_traj).  Any output may be NULL.
+ *
+ * The paper groups the blocks of one trajectory into a "bundle" (Sec. 5); here
+ * thousands of independent networks share one launch.  Each network is assigned
+ * a mapping class by size: one thread per trajectory (M <= thread_max_m), one
+ * warp (M <= warp_max_m), or one block of block_threads threads (M <= 16 *
+ * block_threads).  Work is a list of block-sized tasks (one block-class
+ * trajectory, block_threads/32 warp-class or block_threads thread-class
+ * trajectories), larger networks first, that persistent blocks take from an
+ * atomic counter.  Network i draws its random numbers with stream_id = i, so its
+ * trajectories equal rt_run of that network with stream_id = i.
  */
-int rt_batch_create(int32_t n_nets, const rt_network *const *nets, rt_batch **out);
+typedef struct rt_batch_policy {
+  int32_t thread_max_m;  /* <= 8; networks with more than 8 species go to the warp class */
+  int32_t warp_max_m;    /* <= 256 */
+  int32_t block_threads; /* threads per block: 128 or 256 */
+  int32_t blocks_per_sm; /* persistent blocks per SM; 0 = as many as fit */
+} rt_batch_policy;
+
+/* Pack the networks into one device arena (the batch keeps its own copy; the
+ * network handles may be destroyed afterwards).  policy may be NULL (defaults 8 / 256 / 256 / 0).  All
+ * networks must live on the current device.  Networks too large for the block
+ * class (M > 16 * block_threads) return RT_ERR_UNSUPPORTED. */
+int rt_batch_create(int32_t n_nets, const rt_network *const *nets, const rt_batch_policy *policy, rt_batch **out);
 void rt_batch_destroy(rt_batch *batch);
-int rt_batch_info(const rt_batch *batch, int64_t *total_species, int64_t *total_reactions);
+
+/* Totals of the packed batch: species (length of packed x0), reactions, and the
+ * number of networks in each class (thread, warp, block).  Any pointer may be NULL. */
+int rt_batch_info(const rt_batch *batch, int64_t *total_species, int64_t *total_reactions, int32_t *n_thread_class,
+                  int32_t *n_warp_class, int32_t *n_block_class);
+
+/*
+ * rt_batch_run -- n_traj_per_net trajectories of every network, in one launch
+ * (plus a counter reset), enqueued on `stream` without host synchronisation, so
+ * it can be captured in a CUDA graph.
+ *   x0_dev:    initial counts, network after network (sum of N_i int32)
+ *   t_end_dev: [n_nets] horizons (finite, >= 0)
+ *   outputs (any may be NULL): x_final_dev packed as [net i][traj j][N_i];
+ *   n_events_dev, status_dev, t_last_dev as [net i][traj j].
+ * max_events caps every trajectory (0 <= max_events <= INT32_MAX).
+ */
 int rt_batch_run(rt_batch *batch, const int32_t *x0_dev, const double *t_end_dev, int64_t max_events,
                  uint64_t seed, int64_t n_traj_per_net, int32_t *x_final_dev, int64_t *n_events_dev,
-                 int32_t *status_dev, double *t_last_dev, const rt_launch_cfg *cfg, void *stream);
+                 int32_t *status_dev, double *t_last_dev, void *stream);
 
 /* Message describing the last error on this host thread ("" if none). */
 const char *rt_last_error(void);

@@ -72,7 +72,8 @@ def load(path: str | None = None):
         return _declare(ctypes.CDLL(path))
     with _lock:
         if _lib is None:
-            _lib = _declare(ctypes.CDLL(build()))
+            # ORACLE_LIB points the pins at a variant build (the mutation test uses it)
+            _lib = _declare(ctypes.CDLL(os.environ.get("ORACLE_LIB") or build()))
     return _lib
 
 

@@ -33,7 +33,13 @@
  * the textbook reduction ln(M 2^E) = (E + q) ln 2 + ln(m), m = M / 2^q in
  * [sqrt(1/2), sqrt(2)), and ln(m) = 2 atanh(s), s = (m - 1)/(m + 1), with the
  * atanh power series 2 s (1 + s^2/3 + s^4/5 + ...).
+ *
+ * ORACLE_MUTANT (0 by default) plants one deliberate mistake per value, used only
+ * by the mutation test to show that the pins catch such mistakes.
  */
+#ifndef ORACLE_MUTANT
+#define ORACLE_MUTANT 0
+#endif
 #include <math.h>
 #include <pthread.h>
 #include <stdint.h>
@@ -58,7 +64,7 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
     uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
     uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
     uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
-    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n0 = hi1 ^ (ORACLE_MUTANT == 14 ? c3 : c1) ^ k0;
     uint32_t n1 = lo1;
     uint32_t n2 = hi0 ^ c3 ^ k1;
     uint32_t n3 = lo0;
@@ -137,7 +143,7 @@ static double fx_log(uint64_t M, int E) {
     uint64_t z = mulhi64(s64, s64);                    /* s^2 in Q64 */
     /* F = sum_{i=1..12} z^i / (2i + 1) in Q64, by Horner's rule */
     uint64_t R = 0;
-    for (int i = 12; i >= 1; i--) {
+    for (int i = ORACLE_MUTANT == 12 ? 2 : 12; i >= 1; i--) {
       uint64_t ci = (uint64_t)((((u128)1) << 64) / (u128)(2 * i + 1));
       R = ci + mulhi64(z, R);
     }
@@ -194,7 +200,7 @@ static uint64_t draw_x(uint64_t seed, uint64_t traj, uint32_t k, uint64_t n, uin
   uint32_t w0, w1;
   draw_words(seed, traj, k, n, stream, &w0, &w1);
   uint64_t v = (((uint64_t)w1 << 32) | w0) >> 12;
-  return 2 * v + 1;
+  return ORACLE_MUTANT == 13 ? (v | 1) : 2 * v + 1;
 }
 
 double oracle_uniform(uint64_t seed, uint64_t traj, uint32_t k, uint64_t n, uint32_t stream) {
@@ -269,14 +275,15 @@ static void free_net(onet *g) {
 static int64_t binom(int64_t x, int32_t s) {
   if (x < s) return 0;
   int64_t r = 1;
-  for (int32_t i = 0; i < s; i++) r = r * (x - i) / (i + 1);
+  for (int32_t i = 0; i < s; i++) r = r * (x - i) / (ORACLE_MUTANT == 1 ? 1 : (i + 1));
   return r;
 }
 
 /* a_k = c_k * h_k(X), h_k = prod_j binom(X_j, sigma_jk) (Eq. 1-2) */
 static double propensity(const onet *g, int32_t k, const int32_t *X) {
   int64_t h = 1;
-  for (int64_t i = g->rptr[k]; i < g->rptr[k + 1]; i++) h *= binom(X[g->rsp[i]], g->rcoef[i]);
+  for (int64_t i = g->rptr[k]; i < g->rptr[k + 1]; i++)
+    h *= binom(X[g->rsp[ORACLE_MUTANT == 2 ? g->rptr[k] : i]], g->rcoef[i]);
   return g->c[k] * (double)h;
 }
 
@@ -348,10 +355,10 @@ static void run_traj(const job_t *J, int64_t j, double *P, double *T, double *a,
         if (a[k] == 0.0) {
           w = INFINITY;
         } else {
-          double rem = P[k] - T[k];
+          double rem = P[k] - (ORACLE_MUTANT == 3 ? 0.0 : T[k]);
           w = rem > 0.0 ? rem / a[k] : 0.0;
         }
-        if (w < dmin) { dmin = w; mu = k; }
+        if (ORACLE_MUTANT == 4 ? (w < dmin && mu < 0) : (w < dmin)) { dmin = w; mu = k; }
       }
       if (mu < 0) { status = ST_ABSORBED; break; }
       double tn = t + dmin;
@@ -366,7 +373,8 @@ static void run_traj(const job_t *J, int64_t j, double *P, double *T, double *a,
 
       /* grid points strictly before the event see the pre-event state */
       if (grid)
-        while (gi < J->G && (double)gi * J->sample_dt < tn) {
+        while (gi < J->G && (ORACLE_MUTANT == 10 ? (double)gi * J->sample_dt <= tn + 0.5 * J->sample_dt
+                                                    : (double)gi * J->sample_dt < tn)) {
           memcpy(grid + gi * N, X, sizeof(int32_t) * (size_t)N);
           gi++;
         }
@@ -375,15 +383,23 @@ static void run_traj(const job_t *J, int64_t j, double *P, double *T, double *a,
 
       t = tn;
       /* every internal time advances by a_k dt (Eq. 17) */
-      for (int32_t k = 0; k < M; k++) T[k] = T[k] + a[k] * dmin;
+      if (ORACLE_MUTANT == 5) { /* propensities of the post-event state used for the elapsed step */
+        for (int64_t i = g->vptr[mu]; i < g->vptr[mu + 1]; i++) X[g->vsp[i]] += g->vdel[i];
+        for (int32_t k = 0; k < M; k++) a[k] = propensity(g, k, X);
+        for (int64_t i = g->vptr[mu]; i < g->vptr[mu + 1]; i++) X[g->vsp[i]] -= g->vdel[i];
+      }
+      for (int32_t k = 0; k < M; k++) T[k] = T[k] + a[k] * (ORACLE_MUTANT == 6 ? t : dmin);
       if (J->loglik) ll = ll + oracle_rt_log(a[mu]);
       /* fire: X += v_mu (Eq. 5) */
-      for (int64_t i = g->vptr[mu]; i < g->vptr[mu + 1]; i++) X[g->vsp[i]] += g->vdel[i];
+      for (int64_t i = g->vptr[mu]; i < g->vptr[mu + 1]; i++)
+        X[g->vsp[i]] += (ORACLE_MUTANT == 7 && g->vdel[i] < 0) ? -g->vdel[i] : g->vdel[i];
       if (trace_mu && ev < J->trace_len) { trace_mu[ev] = mu; trace_t[ev] = t; }
       n[mu] += 1;
       ev += 1;
       /* only the fired channel draws a new increment (Eq. 27) */
-      P[mu] = P[mu] + oracle_exp1(J->seed, gid, (uint32_t)mu, (uint64_t)n[mu], J->stream);
+      if (ORACLE_MUTANT == 8) P[mu] = oracle_exp1(J->seed, gid, (uint32_t)mu, (uint64_t)n[mu], J->stream);
+      else P[mu] = P[mu] + oracle_exp1(J->seed, gid, (uint32_t)mu, (uint64_t)(ORACLE_MUTANT == 9 ? 0 : n[mu]),
+                                       J->stream);
       /* propensities from the new state (Eq. 1-2) */
       for (int32_t k = 0; k < M; k++) a[k] = propensity(g, k, X);
     }
@@ -404,7 +420,7 @@ static void run_traj(const job_t *J, int64_t j, double *P, double *T, double *a,
     /* log-likelihood of the path: sum of ln a_mu minus the integrated propensity */
     double sT = 0.0;
     for (int32_t k = 0; k < M; k++) sT = sT + T[k];
-    J->loglik[j] = status == ST_BAD_X0 ? NAN : ll - sT;
+    J->loglik[j] = status == ST_BAD_X0 ? NAN : (ORACLE_MUTANT == 11 ? ll + sT : ll - sT);
   }
   if (J->counts) memcpy(J->counts + j * (int64_t)M, n, sizeof(int32_t) * (size_t)M);
   if (J->t_internal) memcpy(J->t_internal + j * (int64_t)M, T, sizeof(double) * (size_t)M);

@@ -30,6 +30,10 @@ class rt_run_params(ctypes.Structure):
                 ("seed", u64), ("n_traj", i64), ("traj_offset", i64), ("sample_dt", dbl)]
 
 
+class rt_batch_policy(ctypes.Structure):
+    _fields_ = [("thread_max_m", i32), ("warp_max_m", i32), ("block_threads", i32), ("blocks_per_sm", i32)]
+
+
 class rt_outputs(ctypes.Structure):
     _fields_ = [("x_final_dev", vp), ("grid_dev", vp), ("grid_sum_dev", vp), ("grid_sumsq_dev", vp),
                 ("grid_count_dev", vp), ("n_events_dev", vp), ("status_dev", vp), ("t_last_dev", vp),
@@ -50,10 +54,10 @@ SIGNATURES = [
     ("rt_draw_exp1", ctypes.c_int, [u64, u32, i64, vp, vp, vp, vp, vp, vp]),
     ("rt_log_eval", ctypes.c_int, [i64, vp, vp, vp]),
     ("rt_philox", ctypes.c_int, [i64, vp, u32, u32, vp, vp]),
-    ("rt_batch_create", ctypes.c_int, [i32, vp, ctypes.POINTER(vp)]),
+    ("rt_batch_create", ctypes.c_int, [i32, vp, ctypes.POINTER(rt_batch_policy), ctypes.POINTER(vp)]),
     ("rt_batch_destroy", None, [vp]),
-    ("rt_batch_info", ctypes.c_int, [vp, vp, vp]),
-    ("rt_batch_run", ctypes.c_int, [vp, vp, vp, i64, u64, i64, vp, vp, vp, vp, ctypes.POINTER(rt_launch_cfg), vp]),
+    ("rt_batch_info", ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
+    ("rt_batch_run", ctypes.c_int, [vp, vp, vp, i64, u64, i64, vp, vp, vp, vp, vp]),
     ("rt_last_error", ctypes.c_char_p, []),
 ]
 

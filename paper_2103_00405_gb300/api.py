@@ -174,6 +174,87 @@ class LogLik(torch.autograd.Function):
         return g.to(ctx.c_device), None, None, None, None, None, None, None
 
 
+class Batch:
+    """Many networks in one persistent launch (rt_batch_create / rt_batch_run).
+
+    Network i draws its random numbers with stream_id = i, so its trajectories are
+    those of ``simulate(Network(specs[i]), ..., stream_id=i)``.
+    """
+
+    def __init__(self, specs, thread_max_m: int = 8, warp_max_m: int = 256, block_threads: int = 256,
+                 blocks_per_sm: int = 0):
+        self.lib = L.load()
+        nets = [Network(s) for s in specs]
+        arr = (ctypes.c_void_p * len(nets))(*[n.handle.value for n in nets])
+        pol = L.rt_batch_policy(thread_max_m, warp_max_m, block_threads, blocks_per_sm)
+        h = ctypes.c_void_p()
+        L.check(self.lib.rt_batch_create(len(nets), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(pol),
+                                         ctypes.byref(h)), "rt_batch_create")
+        for n in nets:  # the batch keeps its own copy
+            n.close()
+        self.handle = h
+        self.specs = list(specs)
+        self.N = np.array([s.n_species for s in specs], np.int64)
+        self.M = np.array([s.n_reactions for s in specs], np.int64)
+        self.xoff = np.concatenate([[0], np.cumsum(self.N)[:-1]])
+        self.policy = (thread_max_m, warp_max_m, block_threads, blocks_per_sm)
+
+    def info(self):
+        ts, tr = ctypes.c_int64(), ctypes.c_int64()
+        c = [ctypes.c_int32() for _ in range(3)]
+        L.check(self.lib.rt_batch_info(self.handle, ctypes.byref(ts), ctypes.byref(tr), *[ctypes.byref(x) for x in c]),
+                "rt_batch_info")
+        return dict(total_species=ts.value, total_reactions=tr.value, n_thread=c[0].value, n_warp=c[1].value,
+                    n_block=c[2].value)
+
+    def outputs(self, n_traj: int):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        n = len(self.specs)
+        return dict(x_final=torch.empty(int(self.N.sum()) * n_traj, dtype=torch.int32, device=dev),
+                    n_events=torch.empty((n, n_traj), dtype=torch.int64, device=dev),
+                    status=torch.empty((n, n_traj), dtype=torch.int32, device=dev),
+                    t_last=torch.empty((n, n_traj), dtype=torch.float64, device=dev))
+
+    def run(self, x0: torch.Tensor, t_end: torch.Tensor, n_traj: int, seed: int = 1,
+            max_events: int = (1 << 31) - 1, outputs: Optional[dict] = None) -> dict:
+        """x0: packed int32 device tensor (sum of N_i); t_end: float64 device tensor [n_nets]."""
+        out = outputs if outputs is not None else self.outputs(n_traj)
+        L.check(self.lib.rt_batch_run(self.handle, _ptr(x0), _ptr(t_end), int(max_events), int(seed) & (2**64 - 1),
+                                      int(n_traj), _ptr(out["x_final"]), _ptr(out["n_events"]), _ptr(out["status"]),
+                                      _ptr(out["t_last"]), _stream()), "rt_batch_run")
+        return out
+
+    def x_final_of(self, out: dict, i: int, n_traj: int) -> torch.Tensor:
+        """[n_traj, N_i] final states of network i from the packed output."""
+        b = int(self.xoff[i]) * n_traj
+        return out["x_final"][b:b + n_traj * int(self.N[i])].view(n_traj, int(self.N[i]))
+
+    def capture(self, x0: torch.Tensor, t_end: torch.Tensor, n_traj: int, seed: int = 1,
+                max_events: int = (1 << 31) - 1):
+        """Capture one rt_batch_run in a CUDA graph; returns (graph, outputs).  graph.replay() reruns it."""
+        out = self.outputs(n_traj)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run(x0, t_end, n_traj, seed, max_events, out)  # warm-up outside the graph
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run(x0, t_end, n_traj, seed, max_events, out)
+        return g, out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.rt_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def draw_exp1(seed: int, traj, channel, index, stream_id: int = 0):
     """(u, E) of the library's Philox Exp(1) draws for the given (traj, channel, index) triples."""
     lib = L.load()

@@ -203,9 +203,9 @@ def lv_config(n_traj: int = 64):
 
 # Per-trajectory event cap of the ensemble workload.  A Lotka-Volterra trajectory
 # whose predators die out lets the prey grow until int32 overflow (~2^31 events in
-# one thread); typical trajectories to t = 10 fire ~3.1e5 events.  Capped
+# one thread); trajectories to t = 10 fire at most ~3.1e5 events otherwise.  Capped
 # trajectories end with status MAX_EVENTS and are reported, not dropped.
-ENSEMBLE_MAX_EVENTS = 4_000_000
+ENSEMBLE_MAX_EVENTS = 1_000_000
 
 
 def ensemble_configs(n_traj: int = 1 << 20):

@@ -14,6 +14,9 @@ def pytest_configure(config):
 
 
 def cpu_threads():
+    env = os.environ.get("ORACLE_THREADS")
+    if env:
+        return max(1, int(env))
     return max(1, min(16, os.cpu_count() or 1))
 
 
