@@ -173,6 +173,29 @@ int rt_run(const rt_network *net, const rt_run_params *params, const rt_outputs 
            const rt_launch_cfg *cfg, void *workspace_dev, size_t workspace_bytes, void *stream);
 
 /*
+ * rt_run_bundle_noalloc -- rt_run with the bundle mapping (RT_MAP_BUNDLE) that
+ * allocates nothing and needs no workspace from the caller.  The paper has no
+ * counterpart; it exists for callers that cannot call cudaMalloc where they run a
+ * simulation, such as a host application whose device memory is owned by its own
+ * pool allocator, or a latency-critical loop that must stay out of the driver's
+ * allocator (which can synchronise the device).
+ *
+ * Arguments and results are those of rt_run with cfg->mapping = RT_MAP_BUNDLE and
+ * cfg->ctas_per_traj = ctas_per_traj (<= 0: chosen by the library).  The scratch
+ * lives in a fixed 16 MiB device array inside the library, which every GPU that
+ * loads the library holds until the process exits; a run that needs more (about
+ * 28 bytes per channel per trajectory plus a few KB) returns RT_ERR_OOM with a
+ * message, and nothing is enqueued.  The first call on a device looks up that
+ * array's device address (once per device, with the device current); make that
+ * first call before any stream capture.  All calls on a device share the array
+ * and it keeps the last call's contents: calls whose work overlaps on the GPU
+ * (different streams, or threads without ordering) race on it, so order them on
+ * one stream or synchronise between them.
+ */
+int rt_run_bundle_noalloc(const rt_network *net, const rt_run_params *params, const rt_outputs *outputs,
+                          int32_t ctas_per_traj, void *stream);
+
+/*
  * rt_loglik_backward -- gradient of sum_j grad_ll[j] * l_j with respect to the
  * rate constants, from the counts and internal times saved by rt_run:
  *   grad_c[k] = sum_j grad_ll[j] * (n_jk - T_jk(t_end)) / c_k

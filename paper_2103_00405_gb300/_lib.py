@@ -50,6 +50,8 @@ SIGNATURES = [
                                           ctypes.POINTER(sz)]),
     ("rt_run", ctypes.c_int, [vp, ctypes.POINTER(rt_run_params), ctypes.POINTER(rt_outputs),
                               ctypes.POINTER(rt_launch_cfg), vp, sz, vp]),
+    ("rt_run_bundle_noalloc", ctypes.c_int, [vp, ctypes.POINTER(rt_run_params), ctypes.POINTER(rt_outputs), i32,
+                                             vp]),
     ("rt_loglik_backward", ctypes.c_int, [vp, i64, vp, vp, vp, vp, vp]),
     ("rt_draw_exp1", ctypes.c_int, [u64, u32, i64, vp, vp, vp, vp, vp, vp]),
     ("rt_log_eval", ctypes.c_int, [i64, vp, vp, vp]),

@@ -8,7 +8,7 @@
 
 namespace rt {
 
-static int check_device(const rt_network *net) {
+int check_device(const rt_network *net) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return set_error(RT_ERR_CUDA, "cudaGetDevice failed");
   if (dev != net->device)
@@ -24,7 +24,7 @@ static int choose_mapping(const rt_network *net, const rt_launch_cfg *cfg) {
   return RT_MAP_BUNDLE;
 }
 
-static int validate_run(const rt_network *net, const rt_run_params *p, const rt_outputs *o) {
+int validate_run(const rt_network *net, const rt_run_params *p, const rt_outputs *o) {
   if (!net) return set_error(RT_ERR_INVALID_ARG, "rt_run: NULL network");
   if (!p || !o) return set_error(RT_ERR_INVALID_ARG, "rt_run: NULL params or outputs");
   if (p->n_traj < 0) return set_error(RT_ERR_INVALID_ARG, "n_traj must be >= 0");

@@ -24,6 +24,7 @@
 #include <climits>
 #include <cmath>
 #include <cstdlib>
+#include <mutex>
 
 #include "rt_filter.cuh"
 #include "rt_sim.cuh"
@@ -568,4 +569,82 @@ int launch_bundle_mapping(const RunArgs &a, int ctas_per_traj, void *ws, size_t 
   return RT_OK;
 }
 
+// ----------------------------------------------------------------------------------
+// Allocation-free entry point
+//
+// Some callers cannot call cudaMalloc where they run a simulation: a host
+// application whose device memory is owned by its own pool allocator (a direct
+// cudaMalloc would go around its budget), or a latency-critical loop that must not
+// enter the driver's allocator, which can synchronise the device.  rt_run's large-
+// network mapping needs a caller-allocated workspace; rt_run_bundle_noalloc runs
+// the same kernels with their scratch (P, T, a, counts, block minima, barrier
+// counters) in the fixed array below instead.
+//
+// The array is a file-scope __device__ variable: every GPU that loads this library
+// holds kNoAllocScratchBytes of it until the process exits.  In host code the
+// array's name is only a host-side stand-in, so its device address is obtained with
+// cudaGetSymbolAddress, once per device, by the first call on that device (with the
+// device current); that first call should come before any stream capture.  Every
+// call on a device uses the same array and leaves its contents behind; the launch
+// zeroes what must start at zero (the barrier counters) and initialises the rest.
+// Calls whose work overlaps on the GPU (different streams, or threads without
+// ordering) race on the array: order them on one stream or synchronise between them.
+// ----------------------------------------------------------------------------------
+
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mutex;
+static void *g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the scratch array on the current device (set up once per device).
+static int noalloc_scratch(void **out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_error(RT_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= 64) return set_error(RT_ERR_UNSUPPORTED, "device %d: at most 64 devices are supported", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return set_error(RT_ERR_CUDA, "cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return RT_OK;
+}
+
 }  // namespace rt
+
+extern "C" int rt_run_bundle_noalloc(const rt_network *net, const rt_run_params *p, const rt_outputs *o,
+                                     int32_t ctas_per_traj, void *stream) {
+  using namespace rt;
+  clear_error();
+  int rc = validate_run(net, p, o);
+  if (rc) return rc;
+  if ((rc = check_device(net))) return rc;
+  RunArgs a;
+  a.net = net->dev;
+  a.x0 = p->x0_dev;
+  a.per_traj_x0 = p->per_traj_x0 ? 1 : 0;
+  a.stream_id = p->stream_id;
+  a.t_end = p->t_end;
+  a.max_events = (int32_t)p->max_events;
+  a.seed = p->seed;
+  a.n_traj = p->n_traj;
+  a.traj_offset = p->traj_offset;
+  a.sample_dt = p->sample_dt;
+  const bool want_grid = o->grid_dev || o->grid_sum_dev;
+  a.G = want_grid ? rt_grid_len(p->t_end, p->sample_dt) : 0;
+  a.out = *o;
+  const size_t need = bundle_workspace_bytes(net->dev, p->n_traj, ctas_per_traj);
+  if (need > kNoAllocScratchBytes)
+    return set_error(RT_ERR_OOM,
+                     "rt_run_bundle_noalloc: %lld trajectories of %d reactions need %zu bytes of scratch, more than "
+                     "the fixed %zu-byte array; use fewer trajectories per call or rt_run with a workspace",
+                     (long long)p->n_traj, net->dev.M, need, kNoAllocScratchBytes);
+  void *scratch = nullptr;
+  if ((rc = noalloc_scratch(&scratch))) return rc;
+  return launch_bundle_mapping(a, ctas_per_traj, scratch, kNoAllocScratchBytes, (cudaStream_t)stream);
+}

@@ -65,6 +65,10 @@ struct RunArgs {
   rt_outputs out;
 };
 
+// Argument checks shared by the entry points (rt_api.cu).
+int check_device(const rt_network *net);
+int validate_run(const rt_network *net, const rt_run_params *p, const rt_outputs *o);
+
 // Launchers implemented in the .cu files (return RT_OK or an error code).
 int launch_thread_mapping(const RunArgs &a, int block_threads, cudaStream_t s);
 int thread_mapping_max_m();
