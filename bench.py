@@ -53,8 +53,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--t-end", type=float, default=10.0, help="horizon (reduced only for profiling captures)")
     ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg (profiling captures)")
-    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "large"],
-                    help="ensemble (default): LV + birth-death + dimerisation; large: N=1e4, M=1e6, 16 trajectories")
+    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "large", "batched", "grad"],
+                    help="ensemble (default): LV + birth-death + dimerisation; large: N=1e4, M=1e6, 16 trajectories; "
+                         "batched: 4096 uneven networks in one persistent launch; grad: M=64 forward + backward")
+    ap.add_argument("--batch-events", type=int, default=20_000, help="batched workload: event cap per network")
     ap.add_argument("--events", type=int, default=100_000, help="large workload: events per trajectory per step")
     return ap.parse_args()
 
@@ -230,12 +232,146 @@ def run_large(args):
         print(json.dumps(line))
 
 
+def _timed(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms
+
+
+def run_batched(args):
+    """4096 random networks, M ~ U{4..4096}, N = max(1, M/4), c ~ lognormal(0,1), X0 ~ Poisson(50),
+    t_end ~ U[1,10], one trajectory each, capped at --batch-events events: one persistent CUDA-graph
+    launch (policy from the autotuner) against one rt_run launch per network."""
+    import torch
+
+    from paper_2103_00405_gb300 import api, autotune
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    items = W.batched_networks(4096)
+    specs = [it.net for it in items]
+    x0 = torch.from_numpy(np.concatenate([it.x0 for it in items])).to(dev)
+    t_end = torch.tensor([it.t_end for it in items], dtype=torch.float64, device=dev)
+    cap = args.batch_events
+    policy = autotune.tune_batch(specs, x0, t_end, 1, probe_events=max(100, cap // 20))
+    batch = api.Batch(specs, **policy)
+    graph, out = batch.capture(x0, t_end, 1, seed=1, max_events=cap)
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms = _timed(graph.replay, args.steps, args.warmup, stream)
+    clocks = sampler.stop()
+    events = int(out["n_events"].sum().item())
+    value = events / (statistics.mean(ms) / 1e3)
+    # a 512-network subset both ways: one batch launch, and one rt_run launch per network
+    # (stream_id = network index in the subset, so the trajectories are identical), the
+    # per-network launches spread over 8 CUDA streams
+    sub = items[:512]
+    sbatch = api.Batch([it.net for it in sub], **policy)
+    sx0 = torch.from_numpy(np.concatenate([it.x0 for it in sub])).to(dev)
+    st = torch.tensor([it.t_end for it in sub], dtype=torch.float64, device=dev)
+    sgraph, sout = sbatch.capture(sx0, st, 1, seed=1, max_events=cap)
+    ms_sub = _timed(sgraph.replay, args.steps, 1, stream)
+    nets = [api.Network(it.net) for it in sub]
+    x0s = [torch.as_tensor(it.x0, dtype=torch.int32).to(dev) for it in sub]
+    outs = [{} for _ in sub]
+    streams = [torch.cuda.Stream() for _ in range(8)]
+
+    def per_network():
+        for s_ in streams:
+            s_.wait_stream(stream)
+        for i, it in enumerate(sub):
+            with torch.cuda.stream(streams[i % 8]):
+                api.simulate(nets[i], x0s[i], it.t_end, 1, seed=1, stream_id=i, max_events=cap, outputs=outs[i])
+        for s_ in streams:
+            stream.wait_stream(s_)
+
+    ms_plain = _timed(per_network, 1, 1, stream)
+    plain_events = sum(int(o["n_events"].sum().item()) for o in outs)
+    sub_events = int(sout["n_events"].sum().item())
+    assert plain_events == sub_events, (plain_events, sub_events)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batched: 4096 random networks, M~U{4..4096}, N=M/4, c~lognormal(0,1), "
+                                   "X0~Poisson(50), t_end~U[1,10], 1 trajectory each, one persistent graph launch",
+                       "max_events_per_network": cap, "policy": policy, "events_per_step": events},
+            "clocks": clocks, "gpu_launches": len(ms),
+            "subset_512": {"batched_events_per_s": sub_events / (statistics.mean(ms_sub) / 1e3),
+                           "per_network_launches_events_per_s": plain_events / (statistics.mean(ms_plain) / 1e3),
+                           "unit": UNIT, "events": sub_events, "per_network_streams": 8}}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def run_grad(args):
+    """Random network M = 64, N = 16, c ~ lognormal(0, 0.5), X0 ~ Poisson(200), 65536 trajectories to
+    t_end = 5: forward with log-likelihood plus the backward kernel, against the plain forward."""
+    import torch
+
+    from paper_2103_00405_gb300 import api
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = W.grad_config()
+    net, n = cfg["net"], cfg["n_traj"]
+    c = torch.tensor(net.c, dtype=torch.float64, requires_grad=True)
+    netg = api.Network(net)
+    x0 = torch.as_tensor(cfg["x0"], dtype=torch.int32).to(dev)
+    out_plain, out_grad = {}, {}
+    stream = torch.cuda.current_stream()
+    state = {}
+
+    def fwd_bwd():
+        o = api.simulate(netg, x0, cfg["t_end"], n, seed=1, max_events=10**8, grad=True, outputs=out_grad)
+        state["g"] = api.loglik_backward(netg, torch.ones(n, dtype=torch.float64, device=dev), o["counts"],
+                                         o["t_internal"])
+
+    def fwd_plain():
+        api.simulate(netg, x0, cfg["t_end"], n, seed=1, max_events=10**8, outputs=out_plain)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms = _timed(fwd_bwd, args.steps, args.warmup, stream)
+    clocks = sampler.stop()
+    ms_plain = _timed(fwd_plain, args.steps, args.warmup, stream)
+    events = int(out_grad["n_events"].sum().item())
+    assert events == int(out_plain["n_events"].sum().item())
+    line = {"metric": METRIC, "value": events / (statistics.mean(ms) / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "gradient: random network M=64, N=16, c~lognormal(0,0.5), X0~Poisson(200), "
+                                   "65536 trajectories to t_end=5, forward with log-likelihood + backward kernel",
+                       "events_per_step": events},
+            "clocks": clocks, "gpu_launches": 2 * len(ms),
+            "plain_forward": {"value": events / (statistics.mean(ms_plain) / 1e3), "unit": UNIT,
+                              "ms_per_step": statistics.mean(ms_plain)}}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "large":
         return run_large(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "grad":
+        return run_grad(args)
 
     import torch
 

@@ -85,7 +85,8 @@ def simulate(net: Network, x0, t_end: float, n_traj: int, seed: int = 1, stream_
     grid: "none", "traj" (per-trajectory [n_traj, G, N]) or "moments" (sums over
     trajectories of X and X^2 per grid point, plus counts).
     grad: also return loglik [n_traj], counts [n_traj, M], t_internal [n_traj, M].
-    outputs: optional preallocated tensors (same keys) to write into.
+    outputs: optional dict of preallocated tensors (same keys) to write into; missing entries are
+    allocated and added to it.
     """
     lib = L.load()
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -98,7 +99,7 @@ def simulate(net: Network, x0, t_end: float, n_traj: int, seed: int = 1, stream_
     if per and x0t.shape[0] != n_traj:
         raise ValueError("per-trajectory x0 must have n_traj rows")
     G = grid_len(t_end, sample_dt) if grid != "none" else 0
-    out = dict(outputs or {})
+    out = outputs if outputs is not None else {}  # filled in place when the caller passes a dict
 
     def get(name, shape, dtype, zero=False):
         if name not in out:

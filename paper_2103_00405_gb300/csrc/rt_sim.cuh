@@ -56,10 +56,10 @@ __device__ __forceinline__ double waiting_time_rem(double rem, double a) {
   return dbits(rem) > 0 ? __ddiv_rn(rem, a) : 0.0;
 }
 
-// A float upper bound of the exact quotient rem / a (rem > 0, a > 0).
-__device__ __forceinline__ float quot_upper(double rem, double a) {
-  const float al = f32_lower(a);
-  return al > 0.0f ? __fdiv_ru(f32_upper(rem), al) : __int_as_float(0x7F800000);
+// An estimate of the quotient rem / a (rem > 0, a > 0) used only to pick which
+// channel to compute exactly first; the exclusion test below is what is rigorous.
+__device__ __forceinline__ float quot_estimate(double rem, double a) {
+  return __fdividef(f32_upper(rem), f32_lower(a) + 1e-37f);
 }
 
 // True if the exact quotient rem / a is certainly > thr (rem > 0, a > 0).
@@ -67,12 +67,11 @@ __device__ __forceinline__ bool quot_exceeds(double rem, double a, float thr) {
   return f32_lower(rem) > __fmul_ru(thr, f32_upper(a));
 }
 
-// float upper bound of (P - T) / a (0 if P - T may be <= 0)
-__device__ __forceinline__ float wait_upper(double P, double T, double a) {
-  const float rem = __fsub_ru(f32_upper(P), f32_lower(T));
-  if (!(rem > 0.0f)) return 0.0f;
-  const float al = f32_lower(a);
-  return al > 0.0f ? __fdiv_ru(rem, al) : __int_as_float(0x7F800000);
+// An estimate of (P - T) / a used only to choose the candidate that is computed
+// exactly first (any choice gives the same, exact result).
+__device__ __forceinline__ float wait_estimate(double P, double T, double a) {
+  const float rem = f32_upper(P) - f32_lower(T);
+  return rem > 0.0f ? __fdividef(rem, f32_lower(a) + 1e-37f) : 0.0f;
 }
 
 // Register-array element r (runtime) by predicated selects, so arrays indexed with

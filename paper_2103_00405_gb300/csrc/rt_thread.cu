@@ -21,7 +21,7 @@ static size_t moment_smem_bytes(const RunArgs &a) {
   return b <= 96 * 1024 ? b : 0;
 }
 
-template <int MAXM, bool LL>
+template <int MAXM, bool LL, bool EXACT>
 __global__ void __launch_bounds__(128) k_ens_thread(const RunArgs A, const int tend_finite, const int smem_mom) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int M = A.net.M, N = A.net.N, nv = A.net.n_vnz;
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(128) k_ens_thread(const RunArgs A, const int t
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = j < A.n_traj;
   const int B = blockDim.x;
-  if (active) simulate_one<MAXM, LL>(A, S, j, B, tend_finite, smem_mom);
+  if (active) simulate_one<MAXM, LL, EXACT>(A, S, j, B, tend_finite, smem_mom);
   if (smem_mom) {
     __syncthreads();
     for (int64_t i = threadIdx.x; i < GN; i += blockDim.x) {
@@ -59,18 +59,18 @@ __global__ void __launch_bounds__(128) k_ens_thread(const RunArgs A, const int t
 
 int thread_mapping_max_m() { return 16; }
 
-template <int MAXM>
+template <int MAXM, bool EXACT = false>
 static cudaError_t launch_m(const RunArgs &a, int B, cudaStream_t s, int tend_finite) {
   const size_t mom = moment_smem_bytes(a);
   const size_t smem = ((thread_smem_bytes(a.net.M, a.net.N, a.net.n_vnz, B) + 7) & ~(size_t)7) + mom;
   const unsigned grid = (unsigned)((a.n_traj + B - 1) / B);
   const int smem_mom = mom ? 1 : 0;
   if (a.out.loglik_dev) {
-    auto kern = k_ens_thread<MAXM, true>;
+    auto kern = k_ens_thread<MAXM, true, EXACT>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<grid, B, smem, s>>>(a, tend_finite, smem_mom);
   } else {
-    auto kern = k_ens_thread<MAXM, false>;
+    auto kern = k_ens_thread<MAXM, false, EXACT>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<grid, B, smem, s>>>(a, tend_finite, smem_mom);
   }
@@ -85,7 +85,10 @@ int launch_thread_mapping(const RunArgs &a, int B, cudaStream_t s) {
     return set_error(RT_ERR_UNSUPPORTED, "thread mapping: network too large for shared memory");
   const int tend_finite = isfinite(a.t_end) ? 1 : 0;
   cudaError_t e;
-  if (a.net.M <= 4) e = launch_m<4>(a, B, s, tend_finite);
+  if (a.net.M == 1) e = launch_m<1, true>(a, B, s, tend_finite);
+  else if (a.net.M == 2) e = launch_m<2, true>(a, B, s, tend_finite);
+  else if (a.net.M == 3) e = launch_m<3, true>(a, B, s, tend_finite);
+  else if (a.net.M == 4) e = launch_m<4, true>(a, B, s, tend_finite);
   else if (a.net.M <= 8) e = launch_m<8>(a, B, s, tend_finite);
   else if (a.net.M <= 16) e = launch_m<16>(a, B, s, tend_finite);
   else return set_error(RT_ERR_UNSUPPORTED, "thread mapping supports M <= 16 (got %d)", a.net.M);

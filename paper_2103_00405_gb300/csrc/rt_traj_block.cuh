@@ -152,7 +152,7 @@ __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNe
           if (adv && dbits(a[r]) != 0) T[r] = __dadd_rn(T[r], __dmul_rn(a[r], dprev));
           if ((S.bm[k >> 5] >> (k & 31)) & 1u) a[r] = propensity(net.rd[k], net.c[k], xat);
           if (dbits(a[r]) != 0) {
-            const float u = wait_upper(P[r], T[r], a[r]);
+            const float u = wait_estimate(P[r], T[r], a[r]);
             if (kub == INT_MAX || u < ub) {
               ub = u;
               kub = k;

@@ -40,10 +40,11 @@ __device__ __forceinline__ ThreadNet carve_thread_net(unsigned char *base, int M
 }
 
 
-template <int MAXM, bool LL>
+// MAXM: register slots; EXACT: the network has exactly MAXM reactions (loops fully resolved).
+template <int MAXM, bool LL, bool EXACT = false>
 __device__ __forceinline__ void simulate_one(const RunArgs &A, const ThreadNet &S, const int64_t j, const int B,
                                              const int tend_finite, const int smem_mom) {
-  const int M = A.net.M, N = A.net.N;
+  const int M = EXACT ? MAXM : A.net.M, N = A.net.N;
   const int64_t GN = A.G * N;
   int *X = S.X + threadIdx.x;  // X[s] lives at X[s * B]
   auto xat = [&](int s) { return X[s * B]; };
@@ -119,7 +120,7 @@ __device__ __forceinline__ void simulate_one(const RunArgs &A, const ThreadNet &
         rem[k] = 0.0;
         if (k < M && dbits(a[k]) != 0) {
           rem[k] = __dsub_rn(P[k], T[k]);
-          const float ub = dbits(rem[k]) > 0 ? quot_upper(rem[k], a[k]) : 0.0f;
+          const float ub = dbits(rem[k]) > 0 ? quot_estimate(rem[k], a[k]) : 0.0f;
           if (ks < 0 || ub < ub_min) {
             ub_min = ub;
             ks = k;

@@ -104,7 +104,7 @@ __device__ __forceinline__ void warp_trajectory(const RunArgs &A, const WarpNet 
           if (adv && dbits(a[r]) != 0) T[r] = __dadd_rn(T[r], __dmul_rn(a[r], dprev));
           if ((dep >> r) & 1u) a[r] = propensity(net.rd[k], net.c[k], xat);
           if (dbits(a[r]) != 0) {
-            const float u = wait_upper(P[r], T[r], a[r]);
+            const float u = wait_estimate(P[r], T[r], a[r]);
             if (u < ub || kub == INT_MAX) {
               ub = u;
               kub = k;
