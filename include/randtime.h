@@ -234,7 +234,7 @@ int rt_philox(int64_t count, const uint32_t *ctr_dev, uint32_t key0, uint32_t ke
  * The paper groups the blocks of one trajectory into a "bundle" (Sec. 5); here
  * thousands of independent networks share one launch.  Each network is assigned
  * a mapping class by size: one thread per trajectory (M <= thread_max_m), one
- * warp (M <= warp_max_m), or one block of block_threads threads (M <= 16 *
+ * warp (M <= warp_max_m), or one block of block_threads threads (M <= 8 *
  * block_threads).  Work is a list of block-sized tasks (one block-class
  * trajectory, block_threads/32 warp-class or block_threads thread-class
  * trajectories), larger networks first, that persistent blocks take from an
@@ -244,14 +244,14 @@ int rt_philox(int64_t count, const uint32_t *ctr_dev, uint32_t key0, uint32_t ke
 typedef struct rt_batch_policy {
   int32_t thread_max_m;  /* <= 8; networks with more than 8 species go to the warp class */
   int32_t warp_max_m;    /* <= 256 */
-  int32_t block_threads; /* threads per block: 128 or 256 */
+  int32_t block_threads; /* threads per block: 128, 256 or 512 */
   int32_t blocks_per_sm; /* persistent blocks per SM; 0 = as many as fit */
 } rt_batch_policy;
 
 /* Pack the networks into one device arena (the batch keeps its own copy; the
- * network handles may be destroyed afterwards).  policy may be NULL (defaults 8 / 256 / 256 / 0).  All
+ * network handles may be destroyed afterwards).  policy may be NULL (defaults 8 / 256 / 512 / 0).  All
  * networks must live on the current device.  Networks too large for the block
- * class (M > 16 * block_threads) return RT_ERR_UNSUPPORTED. */
+ * class (M > 8 * block_threads) return RT_ERR_UNSUPPORTED. */
 int rt_batch_create(int32_t n_nets, const rt_network *const *nets, const rt_batch_policy *policy, rt_batch **out);
 void rt_batch_destroy(rt_batch *batch);
 

@@ -182,7 +182,7 @@ class Batch:
     those of ``simulate(Network(specs[i]), ..., stream_id=i)``.
     """
 
-    def __init__(self, specs, thread_max_m: int = 8, warp_max_m: int = 256, block_threads: int = 256,
+    def __init__(self, specs, thread_max_m: int = 8, warp_max_m: int = 256, block_threads: int = 512,
                  blocks_per_sm: int = 0):
         self.lib = L.load()
         nets = [Network(s) for s in specs]

@@ -26,6 +26,9 @@ from . import _lib as L
 from . import api
 
 BATCH_CANDIDATES = [
+    dict(thread_max_m=8, warp_max_m=256, block_threads=512),
+    dict(thread_max_m=4, warp_max_m=256, block_threads=512),
+    dict(thread_max_m=8, warp_max_m=128, block_threads=512),
     dict(thread_max_m=8, warp_max_m=256, block_threads=256),
     dict(thread_max_m=8, warp_max_m=128, block_threads=256),
     dict(thread_max_m=8, warp_max_m=64, block_threads=256),

@@ -30,7 +30,7 @@ struct BNet {
   DevNet d;
   int64_t xoff;  // first species of this network in the packed x0 / x_final rows
   int32_t cls;
-  int32_t R;     // register slots (warp: 1,2,4,8; block: 1,2,4,8,16)
+  int32_t R;     // register slots (warp and block: 1, 2, 4 or 8)
 };
 
 struct BatchArgs {
@@ -73,7 +73,7 @@ __device__ __forceinline__ RunArgs item_args(const BatchArgs &B, int net_index, 
   return A;
 }
 
-__global__ void __launch_bounds__(256) k_batch(const BatchArgs B) {
+__global__ void __launch_bounds__(512) k_batch(const BatchArgs B) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long s_task;
   const int tid = threadIdx.x, BT = blockDim.x, W = BT >> 5, warp = tid >> 5;
@@ -97,8 +97,7 @@ __global__ void __launch_bounds__(256) k_batch(const BatchArgs B) {
         case 1: block_trajectory<1, false>(A, net, S, j, tf); break;
         case 2: block_trajectory<2, false>(A, net, S, j, tf); break;
         case 4: block_trajectory<4, false>(A, net, S, j, tf); break;
-        case 8: block_trajectory<8, false>(A, net, S, j, tf); break;
-        default: block_trajectory<16, false>(A, net, S, j, tf); break;
+        default: block_trajectory<8, false>(A, net, S, j, tf); break;
       }
       continue;
     }
@@ -173,14 +172,14 @@ extern "C" int rt_batch_create(int32_t n_nets, const rt_network *const *nets, co
   if (!out) return set_error(RT_ERR_INVALID_ARG, "rt_batch_create: out is NULL");
   *out = nullptr;
   if (n_nets < 1 || !nets) return set_error(RT_ERR_INVALID_ARG, "need at least one network");
-  rt_batch_policy pol{8, 256, 256, 0};
+  rt_batch_policy pol{8, 256, 512, 0};
   if (policy) pol = *policy;
   if (pol.thread_max_m < 0 || pol.thread_max_m > 8)
     return set_error(RT_ERR_INVALID_ARG, "thread_max_m must be in [0, 8]");
   if (pol.warp_max_m < pol.thread_max_m || pol.warp_max_m > 256)
     return set_error(RT_ERR_INVALID_ARG, "warp_max_m must be in [thread_max_m, 256]");
-  if (pol.block_threads != 128 && pol.block_threads != 256)
-    return set_error(RT_ERR_INVALID_ARG, "block_threads must be 128 or 256");
+  if (pol.block_threads != 128 && pol.block_threads != 256 && pol.block_threads != 512)
+    return set_error(RT_ERR_INVALID_ARG, "block_threads must be 128, 256 or 512");
   int dev = 0;
   cudaGetDevice(&dev);
   rt_batch *b = new rt_batch();
@@ -202,17 +201,17 @@ extern "C" int rt_batch_create(int32_t n_nets, const rt_network *const *nets, co
     int cls;
     if (M <= pol.thread_max_m && N <= 8) cls = CLS_THREAD;
     else if (M <= pol.warp_max_m) cls = CLS_WARP;
-    else if (M <= 16 * pol.block_threads) cls = CLS_BLOCK;
+    else if (M <= 8 * pol.block_threads) cls = CLS_BLOCK;
     else {
       delete b;
-      return set_error(RT_ERR_UNSUPPORTED, "network %d has %d reactions; the batch supports up to %d", i, M,
-                       16 * pol.block_threads);
+      return set_error(RT_ERR_UNSUPPORTED, "network %d has %d reactions; this policy supports up to %d (8 per thread)",
+                       i, M, 8 * pol.block_threads);
     }
     int R = 1;
     if (cls == CLS_WARP) R = M <= 32 ? 1 : M <= 64 ? 2 : M <= 128 ? 4 : 8;
     if (cls == CLS_BLOCK) {
       const int need = (M + pol.block_threads - 1) / pol.block_threads;
-      R = need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : 16;
+      R = need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : 8;
       b->maxM_block = std::max(b->maxM_block, M);
       b->maxN_block = std::max(b->maxN_block, N);
     }

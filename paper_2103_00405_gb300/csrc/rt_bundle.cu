@@ -207,10 +207,10 @@ __global__ void __launch_bounds__(kBundleThreads) k_bundle(const BundleArgs B) {
       double besta = 0.0;
       float asum = 0.0f;
       const bool advance = dbits(dprev) != 0;
-      for (int64_t k = k0 + 2 * tid; k < k1; k += 2 * (int64_t)blockDim.x) {
-        const bool two = k + 1 < k1;
-        double2 a2, t2, p2;
-        if (two) {
+      // pairs of channels k, k+1 per thread; the next pair's loads are issued before the
+      // current pair is processed so that two pairs per thread are in flight
+      auto load_pair = [&](int64_t k, double2 &a2, double2 &t2, double2 &p2) {
+        if (k + 1 < k1) {
           a2 = *(const double2 *)(A + k);
           t2 = *(const double2 *)(T + k);
           p2 = __ldcs((const double2 *)(P + k));
@@ -219,6 +219,16 @@ __global__ void __launch_bounds__(kBundleThreads) k_bundle(const BundleArgs B) {
           t2 = make_double2(T[k], 0.0);
           p2 = make_double2(P[k], 0.0);
         }
+      };
+      const int64_t stride = 2 * (int64_t)blockDim.x;
+      int64_t k = k0 + 2 * tid;
+      double2 a2 = make_double2(0.0, 0.0), t2 = a2, p2 = a2;
+      if (k < k1) load_pair(k, a2, t2, p2);
+      for (; k < k1; k += stride) {
+        const int64_t kn = k + stride;
+        double2 a2n = make_double2(0.0, 0.0), t2n = a2n, p2n = a2n;
+        if (kn < k1) load_pair(kn, a2n, t2n, p2n);
+        const bool two = k + 1 < k1;
         double av[2] = {a2.x, a2.y}, tv[2] = {t2.x, t2.y};
         const double pv[2] = {p2.x, p2.y};
         const uint32_t bits = bm[(k - k0) >> 5] >> ((k - k0) & 31);
@@ -247,6 +257,9 @@ __global__ void __launch_bounds__(kBundleThreads) k_bundle(const BundleArgs B) {
           if (two) *(double2 *)(T + k) = make_double2(tv[0], tv[1]);
           else T[k] = tv[0];
         }
+        a2 = a2n;
+        t2 = t2n;
+        p2 = p2n;
       }
 
       // ---- block argmin (lexicographic on (w, k)) and sum of a

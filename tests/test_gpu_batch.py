@@ -37,7 +37,7 @@ def check_against_oracle(items, batch, out, n_traj, max_events, seed):
         assert np.array_equal(out["t_last"][i].cpu().numpy().view(np.int64), o["t_last"].view(np.int64)), i
 
 
-@pytest.mark.parametrize("policy", [dict(), dict(thread_max_m=4, warp_max_m=64, block_threads=128),
+@pytest.mark.parametrize("policy", [dict(), dict(thread_max_m=4, warp_max_m=64, block_threads=256),
                                     dict(thread_max_m=0, warp_max_m=0)])
 def test_batch_bit_exact_per_network(policy):
     items, batch, x0, t_end = make_batch(60, 1200, seed=5, **policy)
