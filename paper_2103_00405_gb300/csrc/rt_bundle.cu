@@ -497,27 +497,37 @@ static BundlePlan plan_bundle(const DevNet &net, int64_t n_traj, int C) {
   return p;
 }
 
-int bundle_max_resident(const DevNet &net, int C, bool ll) {
-  int dev = 0, sms = 0, per_sm = 0;
+// Blocks of the bundle kernel resident on the whole GPU at a given shared-memory size;
+// 0 when the size is above the opt-in limit (checked first, so that no attribute call
+// fails and leaves an error behind for the caller's next CUDA call).
+static int bundle_capacity(size_t smem, bool ll) {
+  int dev = 0, sms = 0, optin = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const BundlePlan p = plan_bundle(net, 1, C);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem > (size_t)optin - 1024) return 0;  // static shared memory (barriers) included
   auto kern = ll ? k_bundle<true> : k_bundle<false>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBundleThreads, p.smem);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBundleThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   return per_sm * sms;
 }
 
+// Blocks per trajectory.  The per-block channel bitmap shrinks as C grows, so the
+// smallest C whose shared memory fits is found first; from there C is raised until
+// the trajectories of one wave fill the GPU (n_traj * C <= capacity), keeping at
+// least 32 channels per block.
 static int choose_C(const DevNet &net, int64_t n_traj, int requested, bool ll) {
   if (requested > 0) return requested;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int cap = bundle_max_resident(net, 1, ll);
+  int c_min = 1, cap = 0;
+  for (; c_min <= 4096; c_min *= 2)
+    if ((cap = bundle_capacity(plan_bundle(net, 1, c_min).smem, ll)) >= c_min) break;
+  if (cap < c_min) return 1;  // nothing fits: the launch reports it
   int64_t C = n_traj > 0 ? cap / std::max<int64_t>(1, std::min<int64_t>(n_traj, cap)) : 1;
-  // at least 32 channels per block
   C = std::min<int64_t>(C, std::max<int64_t>(1, net.M / 32));
-  return (int)std::max<int64_t>(1, C);
+  return (int)std::max<int64_t>(c_min, C);
 }
 
 size_t bundle_workspace_bytes(const DevNet &net, int64_t n_traj, int ctas_per_traj) {
@@ -534,7 +544,9 @@ int launch_bundle_mapping(const RunArgs &a, int ctas_per_traj, void *ws, size_t 
     return set_error(RT_ERR_OOM, "bundle mapping needs %zu bytes of workspace (got %zu)", p.total, ws_bytes);
   if (((uintptr_t)ws & 255) != 0) return set_error(RT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
   if (p.smem > 220 * 1024)
-    return set_error(RT_ERR_UNSUPPORTED, "bundle mapping: %d species do not fit in shared memory", a.net.N);
+    return set_error(RT_ERR_UNSUPPORTED,
+                     "bundle mapping: %d species and %lld channels per block do not fit in shared memory",
+                     a.net.N, (long long)p.chunk);
   char *w = (char *)ws;
   BundleArgs B;
   B.r = a;
@@ -559,12 +571,7 @@ int launch_bundle_mapping(const RunArgs &a, int ctas_per_traj, void *ws, size_t 
   if ((e = cudaGetLastError()) != cudaSuccess) return set_error(RT_ERR_CUDA, "init launch: %s", cudaGetErrorString(e));
 
   auto kern = ll ? k_bundle<true> : k_bundle<false>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-  int per_sm = 0, dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBundleThreads, p.smem);
-  const int64_t cap = (int64_t)per_sm * sms;
+  const int64_t cap = bundle_capacity(p.smem, ll);
   if (cap < C) return set_error(RT_ERR_UNSUPPORTED, "bundle of %d blocks cannot be co-resident (capacity %lld)", C, (long long)cap);
   const int64_t per_wave = cap / C;
   for (int64_t t0 = 0; t0 < a.n_traj; t0 += per_wave) {

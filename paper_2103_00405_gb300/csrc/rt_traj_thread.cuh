@@ -8,6 +8,8 @@
 // reached through generic pointers: shared memory in the single-network kernel,
 // global memory in the batched kernel.
 #pragma once
+#include <cooperative_groups.h>
+
 #include <climits>
 
 #include "rt_sim.cuh"
@@ -21,7 +23,9 @@ struct ThreadNet {
   int2 *vl;
   int *vp;
   int *X;
-  unsigned long long *mom;
+  unsigned long long *mom;  // this block's share of the moment table (smem_mom != 0)
+  int mom_cl;               // blocks in the cluster sharing one table (1: no cluster)
+  int64_t mom_rows;         // grid points per block share: point g lives in block g % mom_cl, row g / mom_cl
 };
 
 // Lays the single-network kernel's shared memory out: c, dep, rd, vl, vp, X, moments.
@@ -45,7 +49,6 @@ template <int MAXM, bool LL, bool EXACT = false>
 __device__ __forceinline__ void simulate_one(const RunArgs &A, const ThreadNet &S, const int64_t j, const int B,
                                              const int tend_finite, const int smem_mom) {
   const int M = EXACT ? MAXM : A.net.M, N = A.net.N;
-  const int64_t GN = A.G * N;
   int *X = S.X + threadIdx.x;  // X[s] lives at X[s * B]
   auto xat = [&](int s) { return X[s * B]; };
   const uint64_t g = (uint64_t)(A.traj_offset + j);
@@ -72,12 +75,20 @@ __device__ __forceinline__ void simulate_one(const RunArgs &A, const ThreadNet &
       for (int s = 0; s < N; ++s) gp[s] = X[s * B];
     }
     if (smem_mom) {
+      // the table is split across the blocks of a cluster (distributed shared memory)
+      unsigned long long *m = S.mom;
+      int64_t row = gidx;
+      if (S.mom_cl > 1) {
+        m = cooperative_groups::this_cluster().map_shared_rank(S.mom, (unsigned)(gidx % S.mom_cl));
+        row = gidx / S.mom_cl;
+      }
+      const int64_t GNl = S.mom_rows * N;
       for (int s = 0; s < N; ++s) {
         const long long x = X[s * B];
-        atomicAdd(S.mom + gidx * N + s, (unsigned long long)x);
-        atomicAdd(S.mom + GN + gidx * N + s, (unsigned long long)(x * x));
+        atomicAdd(m + row * N + s, (unsigned long long)x);
+        atomicAdd(m + GNl + row * N + s, (unsigned long long)(x * x));
       }
-      atomicAdd(S.mom + 2 * GN + gidx, 1ull);
+      atomicAdd(m + 2 * GNl + row, 1ull);
     } else if (A.out.grid_sum_dev) {
       for (int s = 0; s < N; ++s) {
         const long long x = X[s * B];

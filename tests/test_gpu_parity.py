@@ -160,6 +160,21 @@ def test_moments_equal_sums_of_oracle_grids():
     assert np.array_equal(g["grid_count"].cpu().numpy(), np.full(grid.shape[1], 500))
 
 
+@pytest.mark.parametrize("sample_dt", [0.02, 0.01, 0.001])
+def test_cluster_shared_moments_equal_sums_of_oracle_grids(sample_dt):
+    """Grids of 501, 1001 and 10001 points: the moment table is split across clusters of 2, 4 and
+    8 blocks; 300 trajectories leave the last cluster partly without trajectories."""
+    c = W.ensemble_configs(300)[2]
+    netg = api.Network(c["net"])
+    g = api.simulate(netg, c["x0"], 10.0, 300, seed=7, sample_dt=sample_dt, grid="moments",
+                     max_events=c["max_events"])
+    o = oracle.run(c["net"], c["x0"], 10.0, 300, seed=7, sample_dt=sample_dt, want_grid=True, n_threads=16)
+    grid = o["grid"].astype(np.int64)
+    assert np.array_equal(g["grid_sum"].cpu().numpy(), grid.sum(0))
+    assert np.array_equal(g["grid_sumsq"].cpu().numpy(), (grid ** 2).sum(0))
+    assert np.array_equal(g["grid_count"].cpu().numpy(), np.full(grid.shape[1], 300))
+
+
 def test_edge_cases_bit_exact():
     lv = W.lotka_volterra()
     # no trajectories
