@@ -512,7 +512,7 @@ def main():
             "gpu_launches": len(evts),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_OP_PEAK / 1e12, "unit": "TFLOP/s",
                          "frac": achieved * 1e12 / FP64_OP_PEAK, "traffic": None,
-                         "kernel": "k_ens_thread (Lotka-Volterra launch)", "launch_ms": lv_ms[-1],
+                         "kernel": "k_ens_small (Lotka-Volterra launch)", "launch_ms": lv_ms[-1],
                          "fp64_ops_per_event": ops / lv_events,
                          "peak_note": "FP64 pipe: nominal 1.25 TFLOP/s with FMA=2 -> 0.625e12 single ops/s (fallback)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

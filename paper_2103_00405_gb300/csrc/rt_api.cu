@@ -85,7 +85,8 @@ extern "C" int rt_run(const rt_network *net, const rt_run_params *p, const rt_ou
   cudaStream_t s = (cudaStream_t)stream;
   switch (mapping) {
     case RT_MAP_THREAD:
-      return launch_thread_mapping(a, B, s);
+      // networks of <= 4 reactions and <= 4 species: network in the parameter space, X in registers
+      return net->small.ok ? launch_small_mapping(a, net->small, B, s) : launch_thread_mapping(a, B, s);
     case RT_MAP_WARP:
       return launch_warp_mapping(a, B, s);
     case RT_MAP_BLOCK:

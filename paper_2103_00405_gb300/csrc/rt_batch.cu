@@ -139,8 +139,7 @@ __global__ void __launch_bounds__(512) k_batch(const BatchArgs B) {
         S.vp = const_cast<int *>(bn.d.vptr);
         S.X = (int *)smem;
         S.mom = nullptr;
-        S.mom_cl = 1;
-        S.mom_rows = 0;
+        S.mt = mom_table(nullptr, 0, 1);
         simulate_one<8, false>(A, S, j, BT, isfinite(A.t_end) ? 1 : 0, 0);
       }
     }

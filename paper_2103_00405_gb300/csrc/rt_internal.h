@@ -28,6 +28,17 @@ struct DevNet {
   const uint8_t *depw;     // [M][32] (M <= 256 only) bit r of depw[mu*32 + l]: channel l + 32 r depends on mu
 };
 
+// Networks of at most kSmallM reactions and kSmallN species: the whole network by
+// value, for kernels that take it in their parameter space (rt_small.cu).
+constexpr int kSmallM = 4, kSmallN = 4;
+struct SmallNet {
+  int32_t ok;                        // 1 if the network fits
+  int32_t s0[kSmallM], s1[kSmallM];  // reactant descriptor of each channel (as DevNet::rdesc)
+  double c[kSmallM];                 // rate constants
+  uint32_t dep[kSmallM];             // bit k: firing this reaction changes a species channel k reads
+  int32_t delta[kSmallM][kSmallN];   // net change of each species when the reaction fires
+};
+
 }  // namespace rt
 
 struct rt_network {
@@ -41,6 +52,7 @@ struct rt_network {
   std::string host_blob;  // the arena's bytes
   size_t off_rdesc = 0, off_c = 0, off_vptr = 0, off_vlist = 0, off_sptr = 0, off_slist = 0, off_dep = 0;
   size_t off_depw = 0;
+  rt::SmallNet small = {};  // filled when M <= kSmallM and N <= kSmallN
 };
 
 namespace rt {
@@ -71,6 +83,7 @@ int validate_run(const rt_network *net, const rt_run_params *p, const rt_outputs
 
 // Launchers implemented in the .cu files (return RT_OK or an error code).
 int launch_thread_mapping(const RunArgs &a, int block_threads, cudaStream_t s);
+int launch_small_mapping(const RunArgs &a, const SmallNet &net, int block_threads, cudaStream_t s);
 int thread_mapping_max_m();
 size_t bundle_workspace_bytes(const DevNet &net, int64_t n_traj, int ctas_per_traj);
 int launch_warp_mapping(const RunArgs &a, int block_threads, cudaStream_t s);

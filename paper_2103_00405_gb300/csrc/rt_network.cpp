@@ -219,6 +219,17 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
   d.depw = M <= 256 ? (const uint8_t *)(db + g->off_depw) : nullptr;
   g->max_dependents = max_dep;
   g->n_dep_nz = dep_nz;
+  if (M <= kSmallM && N <= kSmallN) {
+    SmallNet &sn = g->small;
+    sn.ok = 1;
+    for (int32_t k = 0; k < M; k++) {
+      sn.s0[k] = rdesc[k].x;
+      sn.s1[k] = rdesc[k].y;
+      sn.c[k] = cc[k];
+      sn.dep[k] = (uint32_t)depmask[k];
+      for (int32_t i = vptr[k]; i < vptr[k + 1]; i++) sn.delta[k][vlist[i].x] = vlist[i].y;
+    }
+  }
   *out = g;
   return RT_OK;
 }

@@ -8,10 +8,9 @@
 // reached through generic pointers: shared memory in the single-network kernel,
 // global memory in the batched kernel.
 #pragma once
-#include <cooperative_groups.h>
-
 #include <climits>
 
+#include "rt_moments.cuh"
 #include "rt_sim.cuh"
 
 namespace rt {
@@ -23,9 +22,8 @@ struct ThreadNet {
   int2 *vl;
   int *vp;
   int *X;
-  unsigned long long *mom;  // this block's share of the moment table (smem_mom != 0)
-  int mom_cl;               // blocks in the cluster sharing one table (1: no cluster)
-  int64_t mom_rows;         // grid points per block share: point g lives in block g % mom_cl, row g / mom_cl
+  unsigned long long *mom;  // start of the moment table share in shared memory
+  MomTable mt;              // the share (smem_mom != 0)
 };
 
 // Lays the single-network kernel's shared memory out: c, dep, rd, vl, vp, X, moments.
@@ -75,20 +73,7 @@ __device__ __forceinline__ void simulate_one(const RunArgs &A, const ThreadNet &
       for (int s = 0; s < N; ++s) gp[s] = X[s * B];
     }
     if (smem_mom) {
-      // the table is split across the blocks of a cluster (distributed shared memory)
-      unsigned long long *m = S.mom;
-      int64_t row = gidx;
-      if (S.mom_cl > 1) {
-        m = cooperative_groups::this_cluster().map_shared_rank(S.mom, (unsigned)(gidx % S.mom_cl));
-        row = gidx / S.mom_cl;
-      }
-      const int64_t GNl = S.mom_rows * N;
-      for (int s = 0; s < N; ++s) {
-        const long long x = X[s * B];
-        atomicAdd(m + row * N + s, (unsigned long long)x);
-        atomicAdd(m + GNl + row * N + s, (unsigned long long)(x * x));
-      }
-      atomicAdd(m + 2 * GNl + row, 1ull);
+      mom_add(S.mt, gidx, N, xat);
     } else if (A.out.grid_sum_dev) {
       for (int s = 0; s < N; ++s) {
         const long long x = X[s * B];

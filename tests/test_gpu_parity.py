@@ -140,6 +140,18 @@ def test_random_small_networks_bit_exact(seed):
     assert_same(g, o)
 
 
+@pytest.mark.parametrize("M,N", [(m, n) for m in range(1, 5) for n in range(1, 6)])
+def test_small_networks_every_shape_bit_exact(M, N):
+    """Every M <= 4 with N <= 4 runs the register kernel (network as a kernel parameter, X in
+    registers); N = 5 the shared-memory thread kernel.  Per-trajectory X0, grids and gradients."""
+    net = W.random_mass_action(N, M, seed=7000 + 10 * M + N, c_sigma=0.8)
+    rng = np.random.default_rng(M * 10 + N)
+    x0 = rng.integers(0, 60, size=(161, N)).astype(np.int32)
+    g, o = run_both(net, x0, 2.0, 161, grad=True, grid=True, seed=M + N, stream_id=3, traj_offset=55,
+                    max_events=20000, sample_dt=0.1)
+    assert_same(g, o)
+
+
 @pytest.mark.parametrize("B", [32, 64, 128])
 def test_block_size_does_not_change_results(B):
     cfg = W.lv_config(100)
