@@ -30,6 +30,35 @@ __device__ __forceinline__ double i64_to_f64(int64_t h) {
   return __longlong_as_double((long long)((((uint64_t)(e + 1023)) << 52) | (mant & 0x000FFFFFFFFFFFFFull)));
 }
 
+// c * h rounded to nearest-even for a finite c >= 0 and an integer 0 <= h < 2^32,
+// with integer instructions: the 85-bit product of c's significand and h is rounded
+// to 53 bits.  Other operands, and products outside the normal range, use the
+// FP64 pipe (identical result: h is exact in binary64).
+__device__ __forceinline__ double mul_rn_pos_u32(double c, int64_t h) {
+  if (h == 0) return 0.0;  // c is finite and >= 0
+  const uint64_t bc = (uint64_t)__double_as_longlong(c);
+  const int ec = (int)(bc >> 52);
+  if (h < 0 || h >= (1ll << 32) || ec == 0 || ec >= 0x7FF) return __dmul_rn(c, i64_to_f64(h));
+  const uint64_t cm = (bc & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+  const uint64_t a0 = (uint64_t)(uint32_t)cm * (uint32_t)h;          // low limb product
+  const uint64_t a1 = (uint64_t)(uint32_t)(cm >> 32) * (uint32_t)h;  // high limb product (< 2^53)
+  const uint64_t lo = a0 + (a1 << 32);
+  const uint64_t hi = (a1 >> 32) + (lo < a0 ? 1u : 0u);  // product = hi 2^64 + lo, < 2^85
+  const int len = hi ? 128 - __clzll(hi) : 64 - __clzll(lo);  // bit length, 53..85
+  const int sh = len - 53;                                    // 0..32
+  if (sh == 0) return __longlong_as_double((long long)(((uint64_t)ec << 52) | (lo & 0x000FFFFFFFFFFFFFull)));
+  uint64_t m = (lo >> sh) | (hi << (64 - sh));
+  const uint64_t rest = lo & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+  m += (rest > half || (rest == half && (m & 1))) ? 1 : 0;
+  int e = ec + sh;
+  if (m >> 53) {
+    m >>= 1;
+    e += 1;
+  }
+  if (e >= 0x7FF) return __dmul_rn(c, i64_to_f64(h));
+  return __longlong_as_double((long long)(((uint64_t)e << 52) | (m & 0x000FFFFFFFFFFFFFull)));
+}
+
 // h_k(X) of Eq. 2 for a descriptor {s0, s1}, exact in int64, then a_k = c_k h_k (Eq. 1).
 template <typename XAt>
 __device__ __forceinline__ double propensity(int2 rd, double c, XAt x) {
@@ -42,7 +71,7 @@ __device__ __forceinline__ double propensity(int2 rd, double c, XAt x) {
     else if (rd.y == RD_DIMER) h = x0 * (x0 - 1) / 2;
     else h = x0 * (int64_t)x(rd.y);
   }
-  return __dmul_rn(c, i64_to_f64(h));
+  return mul_rn_pos_u32(c, h);
 }
 
 // Waiting time (P - T) / a of Eq. 25 for a > 0: 0 if no internal time is left.
