@@ -89,7 +89,7 @@ __global__ void k_bundle_init(const BundleArgs B) {
     B.T[o] = 0.0;
     B.NK[o] = 0;
     B.P[o] = exp1_draw(r.seed, (uint64_t)(r.traj_offset + j), (uint32_t)k, 0u, r.stream_id);
-    B.A[o] = propensity(r.net.rdesc[k], r.net.c[k], [&](int s) { return x0[s]; });
+    B.A[o] = propensity<false>(r.net.rdesc[k], r.net.c[k], [&](int s) { return x0[s]; });
   }
 }
 
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kBundleThreads) k_bundle(const BundleArgs B) {
           if (h == 1 && !two) break;
           if (advance && dbits(av[h]) != 0) tv[h] = __dadd_rn(tv[h], __dmul_rn(av[h], dprev));
           if ((bits >> h) & 1u) {
-            av[h] = propensity(r.net.rdesc[k + h], r.net.c[k + h], xat);
+            av[h] = propensity<false>(r.net.rdesc[k + h], r.net.c[k + h], xat);
             A[k + h] = av[h];
           }
           if (dbits(av[h]) != 0) {

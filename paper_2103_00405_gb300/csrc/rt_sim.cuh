@@ -60,7 +60,10 @@ __device__ __forceinline__ double mul_rn_pos_u32(double c, int64_t h) {
 }
 
 // h_k(X) of Eq. 2 for a descriptor {s0, s1}, exact in int64, then a_k = c_k h_k (Eq. 1).
-template <typename XAt>
+// IMUL: the product on integer instructions (faster where the FP64 pipe is the
+// bottleneck) or on the FP64 pipe (the large-network scan, where the integer code
+// in its loop costs more than it saves); both give the same bits.
+template <bool IMUL = true, typename XAt>
 __device__ __forceinline__ double propensity(int2 rd, double c, XAt x) {
   int64_t h;
   if (rd.x < 0) {
@@ -71,7 +74,7 @@ __device__ __forceinline__ double propensity(int2 rd, double c, XAt x) {
     else if (rd.y == RD_DIMER) h = x0 * (x0 - 1) / 2;
     else h = x0 * (int64_t)x(rd.y);
   }
-  return mul_rn_pos_u32(c, h);
+  return IMUL ? mul_rn_pos_u32(c, h) : __dmul_rn(c, i64_to_f64(h));
 }
 
 // Waiting time (P - T) / a of Eq. 25 for a > 0: 0 if no internal time is left.

@@ -116,7 +116,7 @@ __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNe
     n[r] = 0;
     if (!bad && k < M) {
       P[r] = exp1_draw(A.seed, g, (uint32_t)k, 0u, A.stream_id);
-      a[r] = propensity(net.rd[k], net.c[k], xat);
+      a[r] = propensity<false>(net.rd[k], net.c[k], xat);
     }
   }
   int status = bad ? RT_TRAJ_BAD_X0 : RT_TRAJ_TEND;
@@ -150,7 +150,7 @@ __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNe
         const int k = tid + B * r;
         if (k < M) {
           if (adv && dbits(a[r]) != 0) T[r] = __dadd_rn(T[r], __dmul_rn(a[r], dprev));
-          if ((S.bm[k >> 5] >> (k & 31)) & 1u) a[r] = propensity(net.rd[k], net.c[k], xat);
+          if ((S.bm[k >> 5] >> (k & 31)) & 1u) a[r] = propensity<false>(net.rd[k], net.c[k], xat);
           if (dbits(a[r]) != 0) {
             const float u = wait_estimate(P[r], T[r], a[r]);
             if (kub == INT_MAX || u < ub) {

@@ -78,7 +78,7 @@ __device__ __forceinline__ void warp_trajectory(const RunArgs &A, const WarpNet 
     n[r] = 0;
     if (!bad && k < M) {
       P[r] = exp1_draw(A.seed, g, (uint32_t)k, 0u, A.stream_id);
-      a[r] = propensity(net.rd[k], net.c[k], xat);
+      a[r] = propensity<false>(net.rd[k], net.c[k], xat);
     }
   }
   int status = bad ? RT_TRAJ_BAD_X0 : RT_TRAJ_TEND;
@@ -102,7 +102,7 @@ __device__ __forceinline__ void warp_trajectory(const RunArgs &A, const WarpNet 
         const int k = lane + 32 * r;
         if (k < M) {
           if (adv && dbits(a[r]) != 0) T[r] = __dadd_rn(T[r], __dmul_rn(a[r], dprev));
-          if ((dep >> r) & 1u) a[r] = propensity(net.rd[k], net.c[k], xat);
+          if ((dep >> r) & 1u) a[r] = propensity<false>(net.rd[k], net.c[k], xat);
           if (dbits(a[r]) != 0) {
             const float u = wait_estimate(P[r], T[r], a[r]);
             if (u < ub || kub == INT_MAX) {
