@@ -32,7 +32,8 @@ struct BlockNet {
 // shared-memory scratch of one block trajectory
 struct BlockScratch {
   int *X;           // [N]
-  uint32_t *bm;     // [ceil(M/32)]
+  int *NK;          // [M] firing counts n_k
+  uint32_t *bm;     // [ceil(M/32)] channels whose propensity must be recomputed
   float *red_u;     // [warps]
   int *red_k;       // [warps]
   long long *red_w; // [warps]
@@ -40,11 +41,14 @@ struct BlockScratch {
   double *buf;      // [B] (and the broadcast slots below)
   long long *s_wc;  // candidate's exact waiting time
   double *s_amu;    // propensity of the fired channel
+  double *s_E;      // the fired channel's new Exp(1) increment
+  int *s_over;      // set if the fired reaction would leave the int32 range
 };
 
 __host__ __device__ inline size_t block_scratch_bytes(int M, int N, int B) {
   const int W = B / 32;
-  return (size_t)N * 4 + (size_t)((M + 31) / 32) * 4 + (size_t)W * (4 + 4 + 8 + 4) + (size_t)B * 8 + 16 + 64;
+  return (size_t)N * 4 + (size_t)M * 4 + (size_t)((M + 31) / 32) * 4 + (size_t)W * (4 + 4 + 8 + 4) +
+         (size_t)B * 8 + 32 + 64;
 }
 
 __device__ inline BlockScratch carve_block_scratch(unsigned char *base, int M, int N, int B) {
@@ -54,14 +58,25 @@ __device__ inline BlockScratch carve_block_scratch(unsigned char *base, int M, i
   s.red_w = (long long *)(s.buf + B);
   s.s_wc = s.red_w + W;
   s.s_amu = (double *)(s.s_wc + 1);
-  s.red_u = (float *)(s.s_amu + 1);
+  s.s_E = s.s_amu + 1;
+  s.red_u = (float *)(s.s_E + 1);
   s.red_k = (int *)(s.red_u + W);
   s.red_k2 = s.red_k + W;
-  s.bm = (uint32_t *)(s.red_k2 + W);
+  s.s_over = s.red_k2 + W;
+  s.bm = (uint32_t *)(s.s_over + 1);
   s.X = (int *)(s.bm + (M + 31) / 32);
+  s.NK = s.X + N;
   return s;
 }
 
+// Per event (after the first): phase X, right after the argmin is known, runs three
+// independent pieces at once -- the fired reaction's net change applied to X by one
+// thread per changed species (with the int32 range check), its dependents marked in
+// the bitmap, and its new Exp(1) increment drawn by the last thread of the block --
+// then one barrier; phase Y advances every T_k with the pre-event a_k (Eq. 17),
+// recomputes and unmarks the marked propensities and proposes waiting-time bounds.
+// Grid samples, when an event crosses a grid time, are written from the pre-event X
+// before phase X behind their own barrier.
 template <int R, bool LL>
 __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNet &net, const BlockScratch &S, const int64_t j,
                                  const int tend_finite) {
@@ -73,6 +88,8 @@ __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNe
   int *X = S.X;
   for (int s = tid; s < N; s += B) X[s] = x0[s];
   for (int w = tid; w < nbm; w += B) S.bm[w] = 0u;
+  for (int k = tid; k < M; k += B) S.NK[k] = 0;
+  if (tid == 0) *S.s_over = 0;
   __syncthreads();
   int badl = 0;
   for (int s = tid; s < N; s += B) badl |= X[s] < 0;
@@ -94,34 +111,21 @@ __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNe
     if (tid == 0 && A.out.grid_count_dev) atomicAdd((unsigned long long *)(A.out.grid_count_dev + gidx), 1ull);
   };
 
-  auto mark = [&](int mu, bool set) {
-    for (int i = net.vp[mu]; i < net.vp[mu + 1]; ++i) {
-      const int s = net.vl[i].x;
-      for (int q = net.sptr[s] + tid; q < net.sptr[s + 1]; q += B) {
-        const int ch = net.slist[q];
-        if (set) atomicOr(&S.bm[ch >> 5], 1u << (ch & 31));
-        else S.bm[ch >> 5] = 0u;
-      }
-    }
-  };
-
   double P[R], T[R], a[R];
-  int32_t n[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int k = tid + B * r;
     P[r] = 0.0;
     T[r] = 0.0;
     a[r] = 0.0;
-    n[r] = 0;
     if (!bad && k < M) {
       P[r] = exp1_draw(A.seed, g, (uint32_t)k, 0u, A.stream_id);
       a[r] = propensity<false>(net.rd[k], net.c[k], xat);
     }
   }
   int status = bad ? RT_TRAJ_BAD_X0 : RT_TRAJ_TEND;
-  double t = 0.0, ll = 0.0, dprev = 0.0;
-  int mu_prev = -1;
+  double t = 0.0, ll = 0.0, dmin = 0.0;
+  int mu = -1;  // the last fired channel (uniform)
   int32_t ev = 0;
   int64_t gi = 0;
   double next_g = 0.0;
@@ -129,28 +133,30 @@ __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNe
 
   if (!bad) {
     for (;;) {
-      if (mu_prev >= 0) mark(mu_prev, true);
-      __syncthreads();
-      const bool adv = dbits(dprev) != 0;
-      float ub = __int_as_float(0x7F800000);
-      int kub = INT_MAX;
-      if (mu_prev >= 0 && tid == mu_prev % B) {  // Eq. 27: the fired channel draws its next increment
-        const int rm = mu_prev / B;
-        const int32_t nm = pick<R>(n, rm) + 1;
-        const double E = exp1_draw(A.seed, g, (uint32_t)mu_prev, (uint32_t)nm, A.stream_id);
+      // ---- phase Y: the last firing's bookkeeping, T advance, recompute, bounds
+      const bool fired = mu >= 0;
+      if (fired && tid == mu % B) {  // Eq. 27: the fired channel's new increment
+        const int rm = mu / B;
+        const double E = *S.s_E;
 #pragma unroll
         for (int r = 0; r < R; ++r)
-          if (r == rm) {
-            n[r] = nm;
-            P[r] = __dadd_rn(P[r], E);
-          }
+          if (r == rm) P[r] = __dadd_rn(P[r], E);
       }
+      if (LL && fired && tid == 0) ll = __dadd_rn(ll, rt_ln(*S.s_amu));
+      if (tid == 0) *S.s_over = 0;
+      const bool adv = fired && dbits(dmin) != 0;
+      float ub = __int_as_float(0x7F800000);
+      int kub = INT_MAX;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int k = tid + B * r;
         if (k < M) {
-          if (adv && dbits(a[r]) != 0) T[r] = __dadd_rn(T[r], __dmul_rn(a[r], dprev));
-          if ((S.bm[k >> 5] >> (k & 31)) & 1u) a[r] = propensity<false>(net.rd[k], net.c[k], xat);
+          if (adv && dbits(a[r]) != 0) T[r] = __dadd_rn(T[r], __dmul_rn(a[r], dmin));
+          const uint32_t bit = 1u << (k & 31);
+          if (S.bm[k >> 5] & bit) {
+            a[r] = propensity<false>(net.rd[k], net.c[k], xat);
+            atomicAnd(&S.bm[k >> 5], ~bit);
+          }
           if (dbits(a[r]) != 0) {
             const float u = wait_estimate(P[r], T[r], a[r]);
             if (kub == INT_MAX || u < ub) {
@@ -188,6 +194,7 @@ __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNe
         status = RT_TRAJ_ABSORBED;
         break;
       }
+      // ---- the best candidate exactly, then every channel not certified larger (Eq. 25-26)
       if (tid == (kub % B)) {
         const int rs = kub / B;
         *S.s_wc = dbits(waiting_time(pick<R>(P, rs), pick<R>(T, rs), pick<R>(a, rs)));
@@ -232,11 +239,8 @@ __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNe
           bk = k2;
         }
       }
-      const int mu = bk;
-      if (LL && tid == (mu % B)) *S.s_amu = pick<R>(a, mu / B);
-      if (mu_prev >= 0) mark(mu_prev, false);  // bits were read before the last barrier
-      const double dmin = bitsd(bw);
-      const double tn = __dadd_rn(t, dmin);
+      const double dnext = bitsd(bw);
+      const double tn = __dadd_rn(t, dnext);
       if (dbits(tn) > tend_bits) {
         status = RT_TRAJ_TEND;
         break;
@@ -245,31 +249,61 @@ __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNe
         status = RT_TRAJ_MAX_EVENTS;
         break;
       }
-      bool over = false;
-      for (int i = net.vp[mu]; i < net.vp[mu + 1]; ++i) {
+      const int vb = net.vp[bk], ve = net.vp[bk + 1];
+      if (gi < A.G && dbits(next_g) < dbits(tn)) {
+        // grid samples from the pre-event X, after the range check (an overflowing event
+        // records nothing); X is only read until the barrier below
+        bool over = false;
+        for (int i = vb; i < ve; ++i) {
+          const int2 e = net.vl[i];
+          const long long nx = (long long)X[e.x] + e.y;
+          over |= (nx > INT_MAX) | (nx < 0);
+        }
+        if (over) {
+          status = RT_TRAJ_OVERFLOW;
+          break;
+        }
+        while (gi < A.G && dbits(next_g) < dbits(tn)) {
+          record(gi, true);
+          ++gi;
+          next_g = __dmul_rn(__ll2double_rn(gi), A.sample_dt);
+        }
+        __syncthreads();
+      }
+      // ---- phase X: net change with range check, dependents, new draw (all at once)
+      for (int i = vb + tid; i < ve; i += B) {
         const int2 e = net.vl[i];
         const long long nx = (long long)X[e.x] + e.y;
-        over |= (nx > INT_MAX) | (nx < 0);
+        if ((nx > INT_MAX) | (nx < 0)) *S.s_over = 1;
+        X[e.x] = (int)(uint32_t)((uint32_t)X[e.x] + (uint32_t)e.y);
       }
-      if (over) {
+      for (int i = vb; i < ve; ++i) {
+        const int s = net.vl[i].x;
+        for (int q = net.sptr[s] + tid; q < net.sptr[s + 1]; q += B) {
+          const int ch = net.slist[q];
+          atomicOr(&S.bm[ch >> 5], 1u << (ch & 31));
+        }
+      }
+      if (tid == B - 1) {
+        const int32_t n = S.NK[bk] + 1;
+        S.NK[bk] = n;
+        *S.s_E = exp1_draw(A.seed, g, (uint32_t)bk, (uint32_t)n, A.stream_id);
+      }
+      if (LL && tid == (bk % B)) *S.s_amu = pick<R>(a, bk / B);
+      __syncthreads();
+      if (*S.s_over) {  // undo: the event does not fire
+        for (int i = vb + tid; i < ve; i += B) {
+          const int2 e = net.vl[i];
+          X[e.x] = (int)(uint32_t)((uint32_t)X[e.x] - (uint32_t)e.y);
+        }
+        if (tid == B - 1) S.NK[bk] -= 1;
         status = RT_TRAJ_OVERFLOW;
         break;
       }
-      while (gi < A.G && dbits(next_g) < dbits(tn)) {
-        record(gi, true);
-        ++gi;
-        next_g = __dmul_rn(__ll2double_rn(gi), A.sample_dt);
-      }
       t = tn;
-      __syncthreads();  // all reads of X and of the amu slot for this event are done
-      if (LL && tid == 0) ll = __dadd_rn(ll, rt_ln(*S.s_amu));
-      for (int i = net.vp[mu] + tid; i < net.vp[mu + 1]; i += B) {
-        const int2 e = net.vl[i];
-        X[e.x] += e.y;
-      }
       ++ev;
-      dprev = dmin;
-      mu_prev = mu;
+      dmin = dnext;
+      mu = bk;
     }
   }
 
@@ -301,9 +335,7 @@ __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNe
     }
   }
   if (A.out.counts_dev)
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-      if (tid + B * r < M) A.out.counts_dev[j * M + tid + B * r] = n[r];
+    for (int k = tid; k < M; k += B) A.out.counts_dev[j * M + k] = S.NK[k];
   if (A.out.x_final_dev)
     for (int s = tid; s < N; s += B) A.out.x_final_dev[j * N + s] = X[s];
   if (tid == 0) {
