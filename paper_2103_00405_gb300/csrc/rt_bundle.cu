@@ -206,6 +206,7 @@ __global__ void __launch_bounds__(kBundleThreads) k_bundle(const BundleArgs B) {
       int bestk = -1;
       double besta = 0.0;
       float asum = 0.0f;
+      float thr = tau;  // min(tau, float upper bound of the running best)
       const bool advance = dbits(dprev) != 0;
       // pairs of channels k, k+1 per thread; the next pair's loads are issued before the
       // current pair is processed so that two pairs per thread are in flight
@@ -242,13 +243,13 @@ __global__ void __launch_bounds__(kBundleThreads) k_bundle(const BundleArgs B) {
           }
           if (dbits(av[h]) != 0) {
             asum = __fadd_rn(asum, f32_lower(av[h]));
-            const float thr = fminf(tau, bestb == kInfBits ? tau : f32_upper(bitsd(bestb)));
             if (!exceeds(pv[h], tv[h], av[h], thr)) {
               const long long wb = dbits(waiting_time(pv[h], tv[h], av[h]));
               if (wb < bestb) {
                 bestb = wb;
                 bestk = (int)(k + h);
                 besta = av[h];
+                thr = fminf(tau, f32_upper(bitsd(wb)));
               }
             }
           }

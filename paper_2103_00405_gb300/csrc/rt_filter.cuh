@@ -15,22 +15,23 @@
 
 namespace rt {
 
-// largest float <= x for a double x >= 0 (0 below FLT_MIN, FLT_MAX above it)
+// Float bounds from the high word hi of a non-negative double: the float with the
+// same exponent and the top 20 fraction bits is hi * 8 - 0xC0000000 (mod 2^32) when
+// the exponent is in the float's normal range (the exponent field moves from bit 20
+// to bit 23 and is re-biased by 1023 - 127 = 896; 896 * 2^23 = 0xC0000000 mod 2^32).
+
+// largest float <= x for a double x >= 0 (0 below FLT_MIN, just under FLT_MAX above it)
 __device__ __forceinline__ float f32_lower(double x) {
-  const uint32_t hi = (uint32_t)((uint64_t)__double_as_longlong(x) >> 32);
-  const int e = (int)(hi >> 20) - 1023 + 127;
-  if (e <= 0) return 0.0f;
-  if (e >= 255) return 3.4028234663852886e38f;
-  return __uint_as_float(((uint32_t)e << 23) | ((hi & 0xFFFFFu) << 3));
+  const uint32_t hi = (uint32_t)__double2hiint(x);
+  const uint32_t h = min(hi, 0x47EFFFFFu);  // exponent field 1150: the float range's top
+  return hi < (897u << 20) ? 0.0f : __uint_as_float(h * 8u - 0xC0000000u);
 }
 
 // a float >= x for a double x >= 0 (FLT_MIN below it, +inf above FLT_MAX)
 __device__ __forceinline__ float f32_upper(double x) {
-  const uint32_t hi = (uint32_t)((uint64_t)__double_as_longlong(x) >> 32);
-  const int e = (int)(hi >> 20) - 1023 + 127;
-  if (e <= 0) return 1.17549435e-38f;
-  if (e >= 255) return __int_as_float(0x7F800000);
-  return __uint_as_float((((uint32_t)e << 23) | ((hi & 0xFFFFFu) << 3)) + 8u);  // + one 2^-20 unit
+  const uint32_t hi = (uint32_t)__double2hiint(x);
+  const uint32_t f = (max(hi, 897u << 20) * 8u - 0xC0000000u) + 8u;  // + one 2^-20 unit
+  return hi >= (1151u << 20) ? __int_as_float(0x7F800000) : __uint_as_float(f);
 }
 
 // True if the exact (P - T) / a is certainly > thr (a > 0, T >= 0, thr >= 0).
