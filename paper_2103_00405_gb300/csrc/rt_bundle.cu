@@ -33,6 +33,7 @@ namespace rt {
 
 constexpr int kBundleThreads = 512;
 constexpr float kThresholdK = 12.0f;  // per-event threshold K / sum(a): P(re-scan) ~ e^-12
+constexpr int kSumEvery = 64;         // events between two sums of a (the threshold's sum(a))
 
 struct __align__(16) Partial {
   long long wbits;  // bits of the block's minimum waiting time (+inf if none)
@@ -150,6 +151,7 @@ __global__ void __launch_bounds__(kBundleThreads) k_bundle(const BundleArgs B) {
   int status = bad ? RT_TRAJ_BAD_X0 : RT_TRAJ_TEND;
   unsigned long long rounds = 0;
   float tau = __int_as_float(0x7F800000);
+  float tau_last = __int_as_float(0x7F800000);  // block thread 0: K / sum(a) at the last summed event
   int64_t gi = 0;
   double next_g = 0.0;
   const int64_t tend_bits = dbits(r.t_end);
@@ -207,6 +209,9 @@ __global__ void __launch_bounds__(kBundleThreads) k_bundle(const BundleArgs B) {
       double besta = 0.0;
       float asum = 0.0f;
       float thr = tau;  // min(tau, float upper bound of the running best)
+      // sum(a) drifts slowly (an event changes few propensities): it is taken on every
+      // kSumEvery-th event only, and the threshold K / sum(a) is kept in between
+      const bool summed = (ev % kSumEvery) == 0;
       const bool advance = dbits(dprev) != 0;
       // pairs of channels k, k+1 per thread; the next pair's loads are issued before the
       // current pair is processed so that two pairs per thread are in flight
@@ -242,7 +247,7 @@ __global__ void __launch_bounds__(kBundleThreads) k_bundle(const BundleArgs B) {
             A[k + h] = av[h];
           }
           if (dbits(av[h]) != 0) {
-            asum = __fadd_rn(asum, f32_lower(av[h]));
+            if (summed) asum = __fadd_rn(asum, f32_lower(av[h]));
             if (!exceeds(pv[h], tv[h], av[h], thr)) {
               const long long wb = dbits(waiting_time(pv[h], tv[h], av[h]));
               if (wb < bestb) {
@@ -310,7 +315,7 @@ __global__ void __launch_bounds__(kBundleThreads) k_bundle(const BundleArgs B) {
       reduce_and_publish(bestb, bestk, besta, asum);
 
       // ---- meet the other blocks of this trajectory; every block takes the same decision
-      bool rescan_needed;
+      bool rescan_needed, rescanning = false;
       for (;;) {
         if (tid == 0) {
           bool ok = true;
@@ -336,6 +341,7 @@ __global__ void __launch_bounds__(kBundleThreads) k_bundle(const BundleArgs B) {
                 a = ai;
               }
             }
+            if (summed && !rescanning) tau_last = s > 0.0f ? __fdiv_ru(kThresholdK, s) : __int_as_float(0x7F800000);
             // a threshold-filtered scan is exact only if its minimum is below the threshold
             const bool filtered = tau != __int_as_float(0x7F800000);
             if (filtered && !(w < dbits((double)tau))) {
@@ -344,7 +350,7 @@ __global__ void __launch_bounds__(kBundleThreads) k_bundle(const BundleArgs B) {
               dec.mu = k;
               dec.dt = bitsd(w);
               dec.a_mu = a;
-              dec.tau = s > 0.0f ? __fdiv_ru(kThresholdK, s) : __int_as_float(0x7F800000);
+              dec.tau = tau_last;
             }
           }
         }
@@ -353,6 +359,7 @@ __global__ void __launch_bounds__(kBundleThreads) k_bundle(const BundleArgs B) {
         rescan_needed = dec.rescan != 0;
         if (!rescan_needed || dec.stop) break;
         // read-only exact re-scan of the (already advanced) slice
+        rescanning = true;
         tau = __int_as_float(0x7F800000);
         bestb = kInfBits;
         bestk = -1;
