@@ -34,6 +34,7 @@ namespace rt {
 constexpr int kBundleThreads = 512;
 constexpr float kThresholdK = 12.0f;  // per-event threshold K / sum(a): P(re-scan) ~ e^-12
 constexpr int kSumEvery = 64;         // events between two sums of a (the threshold's sum(a))
+constexpr int kMaxDepth = 6;          // stages of the per-thread copy ring, at most
 
 struct __align__(16) Partial {
   long long wbits;  // bits of the block's minimum waiting time (+inf if none)
@@ -57,6 +58,7 @@ struct BundleArgs {
   int tend_finite;
   long long spin_limit;
   int want_T;        // finalise T at t_end (t_internal or loglik requested)
+  int depth;         // stages of the per-thread copy ring, 1..kMaxDepth
 };
 
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
@@ -94,6 +96,24 @@ __global__ void k_bundle_init(const BundleArgs B) {
   }
 }
 
+// ---- per-thread asynchronous global -> shared copies (16 B) in commit groups ----
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most n of this thread's most recent groups are pending (n < kMaxDepth)
+__device__ __forceinline__ void cp_async_wait(int n) {
+  switch (n) {
+    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+    case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+    case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
+  }
+}
+
 struct Decision {
   int mu;
   int stop;      // 0 continue, else 1 + status
@@ -122,7 +142,9 @@ __global__ void __launch_bounds__(kBundleThreads) k_bundle(const BundleArgs B) {
   const int64_t k0 = (int64_t)c * B.chunk;
   const int64_t k1 = min((int64_t)M, k0 + B.chunk);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int *Xs = (int *)smem;
+  const int D = B.depth;
+  double *ring = (double *)smem;  // [D][3][kBundleThreads][2]: P, T, a pairs of each thread
+  int *Xs = (int *)(ring + (size_t)D * 3 * 2 * kBundleThreads);
   uint32_t *bm = (uint32_t *)(Xs + N);
   const int nbm = (int)((B.chunk + 31) / 32);
   double *P = B.P + j * B.Ms, *T = B.T + j * B.Ms, *A = B.A + j * B.Ms;
@@ -213,27 +235,35 @@ __global__ void __launch_bounds__(kBundleThreads) k_bundle(const BundleArgs B) {
       // kSumEvery-th event only, and the threshold K / sum(a) is kept in between
       const bool summed = (ev % kSumEvery) == 0;
       const bool advance = dbits(dprev) != 0;
-      // pairs of channels k, k+1 per thread; the next pair's loads are issued before the
-      // current pair is processed so that two pairs per thread are in flight
-      auto load_pair = [&](int64_t k, double2 &a2, double2 &t2, double2 &p2) {
-        if (k + 1 < k1) {
-          a2 = *(const double2 *)(A + k);
-          t2 = *(const double2 *)(T + k);
-          p2 = __ldcs((const double2 *)(P + k));
-        } else {
-          a2 = make_double2(A[k], 0.0);
-          t2 = make_double2(T[k], 0.0);
-          p2 = make_double2(P[k], 0.0);
-        }
-      };
+      // pairs of channels k, k+1 per thread.  Each thread streams its own pairs through
+      // a ring of D shared-memory stages filled by asynchronous copies, so D - 1 pairs
+      // per thread are in flight while one is processed, without holding registers.
+      // A pair is copied as 16 bytes even when only k is in the slice: then k + 1 = M
+      // is the row's padding (rows are padded to a multiple of 32) and is not used.
       const int64_t stride = 2 * (int64_t)blockDim.x;
-      int64_t k = k0 + 2 * tid;
-      double2 a2 = make_double2(0.0, 0.0), t2 = a2, p2 = a2;
-      if (k < k1) load_pair(k, a2, t2, p2);
-      for (; k < k1; k += stride) {
-        const int64_t kn = k + stride;
-        double2 a2n = make_double2(0.0, 0.0), t2n = a2n, p2n = a2n;
-        if (kn < k1) load_pair(kn, a2n, t2n, p2n);
+      const int64_t kb = k0 + 2 * tid;
+      const int nmine = kb < k1 ? (int)((k1 - kb + stride - 1) / stride) : 0;
+      auto slot = [&](int st, int arr) { return ring + ((size_t)(st * 3 + arr) * kBundleThreads + tid) * 2; };
+      int st_issue = 0, st_use = 0;
+      auto issue = [&](int i) {  // pair i of this thread, one commit group (empty past the end)
+        if (i < nmine) {
+          const int64_t kk = kb + (int64_t)i * stride;
+          cp_async16(slot(st_issue, 0), P + kk);
+          cp_async16(slot(st_issue, 1), T + kk);
+          cp_async16(slot(st_issue, 2), A + kk);
+        }
+        cp_async_commit();
+        st_issue = st_issue + 1 == D ? 0 : st_issue + 1;
+      };
+      for (int i = 0; i < D - 1; ++i) issue(i);
+      for (int i = 0; i < nmine; ++i) {
+        issue(i + D - 1);  // into the stage processed in the previous iteration
+        cp_async_wait(D - 1);
+        const int64_t k = kb + (int64_t)i * stride;
+        const double2 a2 = *(const double2 *)slot(st_use, 2);
+        const double2 t2 = *(const double2 *)slot(st_use, 1);
+        const double2 p2 = *(const double2 *)slot(st_use, 0);
+        st_use = st_use + 1 == D ? 0 : st_use + 1;
         const bool two = k + 1 < k1;
         double av[2] = {a2.x, a2.y}, tv[2] = {t2.x, t2.y};
         const double pv[2] = {p2.x, p2.y};
@@ -263,10 +293,8 @@ __global__ void __launch_bounds__(kBundleThreads) k_bundle(const BundleArgs B) {
           if (two) *(double2 *)(T + k) = make_double2(tv[0], tv[1]);
           else T[k] = tv[0];
         }
-        a2 = a2n;
-        t2 = t2n;
-        p2 = p2n;
       }
+      cp_async_wait(0);  // only empty groups can remain; none is left behind
 
       // ---- block argmin (lexicographic on (w, k)) and sum of a
       auto reduce_and_publish = [&](long long wb, int kk, double aa, float ss) {
@@ -485,7 +513,12 @@ struct BundlePlan {
   int64_t Ms, chunk;
   size_t off_P, off_T, off_A, off_NK, off_part, off_bar, total;
   size_t smem;
+  int depth;  // stages of the per-thread copy ring
 };
+
+constexpr int kRingDepth = 4;               // preferred ring depth (3 pairs per thread in flight)
+constexpr size_t kSmemBudget = 220 * 1024;  // dynamic shared memory per block
+static_assert(kRingDepth <= kMaxDepth, "ring deeper than cp_async_wait supports");
 
 static BundlePlan plan_bundle(const DevNet &net, int64_t n_traj, int C) {
   BundlePlan p;
@@ -501,7 +534,17 @@ static BundlePlan plan_bundle(const DevNet &net, int64_t n_traj, int C) {
   p.off_part = off; off += (size_t)round_up(rows * 2 * C * sizeof(Partial), 256);
   p.off_bar = off; off += (size_t)round_up(rows * sizeof(unsigned long long), 256);
   p.total = off;
-  p.smem = (size_t)net.N * 4 + (size_t)((p.chunk + 31) / 32) * 4;
+  const size_t rest = (size_t)net.N * 4 + (size_t)((p.chunk + 31) / 32) * 4;
+  const size_t stage = (size_t)3 * 2 * kBundleThreads * 8;  // 24 KB per ring stage
+  int want = kRingDepth;  // RT_BUNDLE_RING_DEPTH (1..kMaxDepth) overrides, for tuning
+  if (const char *env = getenv("RT_BUNDLE_RING_DEPTH")) want = std::min(kMaxDepth, std::max(1, atoi(env)));
+  p.depth = 1;
+  for (int d = want; d > 1; --d)
+    if (d * stage + rest <= kSmemBudget) {
+      p.depth = d;
+      break;
+    }
+  p.smem = p.depth * stage + rest;
   return p;
 }
 
@@ -551,7 +594,7 @@ int launch_bundle_mapping(const RunArgs &a, int ctas_per_traj, void *ws, size_t 
   if (!ws || ws_bytes < p.total)
     return set_error(RT_ERR_OOM, "bundle mapping needs %zu bytes of workspace (got %zu)", p.total, ws_bytes);
   if (((uintptr_t)ws & 255) != 0) return set_error(RT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
-  if (p.smem > 220 * 1024)
+  if (p.smem > kSmemBudget)
     return set_error(RT_ERR_UNSUPPORTED,
                      "bundle mapping: %d species and %lld channels per block do not fit in shared memory",
                      a.net.N, (long long)p.chunk);
@@ -569,6 +612,7 @@ int launch_bundle_mapping(const RunArgs &a, int ctas_per_traj, void *ws, size_t 
   B.bar = (unsigned long long *)(w + p.off_bar);
   B.tend_finite = std::isfinite(a.t_end) ? 1 : 0;
   B.want_T = (a.out.t_internal_dev || a.out.loglik_dev) ? 1 : 0;
+  B.depth = p.depth;
   long long spin = 20000000;  // ~2 s of 100 ns polls
   if (const char *env = getenv("RT_DEBUG_SPIN_LIMIT")) spin = atoll(env);
   B.spin_limit = spin;
