@@ -4,7 +4,8 @@
 // thread per reaction and a two-level (block, then bundle) argmin reduction.  Here a
 // trajectory's M channels are split into C contiguous slices, one per co-resident
 // block (cooperative launch); per event every block streams its slice of P, T, a
-// through HBM with 16-byte loads in one fused pass:
+// through HBM in one fused pass (16-byte asynchronous copies into a per-thread ring
+// of shared-memory stages, several pairs of channels per thread in flight):
 //   T_k += a_k * dt_prev                       (Eq. 17, with the pre-event a_k)
 //   a_k = c_k h_k(X) if k depends on a species the last event changed (Eq. 1-2)
 //   w_k = (P_k - T_k) / a_k and a running argmin (Eq. 25-26)
@@ -14,9 +15,9 @@
 //
 // The exact binary64 division is skipped for channels whose certified float lower
 // bound exceeds a threshold: the block's running best, and a per-event threshold
-// K / sum(a) that catches all but ~e^-K of minima.  If no channel beat the
-// threshold, the event is re-scanned without it (read-only), so the minimum is always
-// the exact one, with the smallest index on ties.
+// K / sum(a) that catches all but ~e^-K of minima (sum(a) retaken every 64 events).
+// If no channel beat the threshold, the event is re-scanned without it (read-only),
+// so the minimum is always the exact one, with the smallest index on ties.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
