@@ -184,19 +184,38 @@ __device__ __forceinline__ void warp_trajectory(const RunArgs &A, const WarpNet 
         next_g = __dmul_rn(__ll2double_rn(gi), A.sample_dt);
       }
       t = tn;
+      // The fired channel's new Exp(1) increment (Eq. 27) is -ln u and, with the
+      // likelihood, ln a_mu is needed too: the owner lane and its neighbour prepare
+      // their arguments, then run one fixed-point logarithm side by side.
+      const int lmu = mu & 31, rm = mu >> 5, lll = lmu ^ 1;
+      const double amu = LL ? __shfl_sync(0xFFFFFFFFu, pick<R>(a, rm), lmu) : 0.0;
+      uint64_t lm = 1;
+      int le = 0;
+      int32_t nm = 0;
+      if (lane == lmu) {
+        nm = pick<R>(n, rm) + 1;
+        lm = bits_to_x(draw_bits(A.seed, g, (uint32_t)mu, (uint32_t)nm, A.stream_id));
+        le = -53;
+      } else if (LL && lane == lll) {
+        const uint64_t b = (uint64_t)__double_as_longlong(amu);
+        const int ef = (int)((b >> 52) & 0x7FF);
+        const uint64_t frac = b & 0x000FFFFFFFFFFFFFull;
+        lm = ef == 0 ? frac : (frac | (1ull << 52));
+        le = ef == 0 ? -1074 : ef - 1075;
+      }
+      double L = 0.0;
+      if (lane == lmu || (LL && lane == lll)) L = fx_ln(lm, le);
       if (LL) {
-        const double amu = __shfl_sync(0xFFFFFFFFu, pick<R>(a, mu >> 5), mu & 31);
-        if (lane == 0) ll = __dadd_rn(ll, rt_ln(amu));
+        const double lv = __shfl_sync(0xFFFFFFFFu, L, lll);
+        if (lane == 0) ll = __dadd_rn(ll, lv);
       }
       __syncwarp();
       for (int i = vb + lane; i < ve; i += 32) {
         const int2 e = net.vl[i];
         X[e.x] += e.y;
       }
-      if (lane == (mu & 31)) {
-        const int rm = mu >> 5;
-        const int32_t nm = pick<R>(n, rm) + 1;
-        const double E = exp1_draw(A.seed, g, (uint32_t)mu, (uint32_t)nm, A.stream_id);
+      if (lane == lmu) {
+        const double E = -L;
 #pragma unroll
         for (int r = 0; r < R; ++r)
           if (r == rm) {
