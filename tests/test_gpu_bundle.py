@@ -56,6 +56,20 @@ def test_bundle_grid_and_likelihood_to_finite_horizon(mid):
     assert_same(g, o)
 
 
+@pytest.mark.parametrize("n_species", [20000, 40000, 48000])
+def test_bundle_copy_ring_depths_fall_back_with_many_species(n_species):
+    """Each block mirrors X in shared memory, so many species leave less room for the copy
+    ring: 20000 species keep 4 stages, 40000 leave 2 and 48000 one (no copy in flight while a
+    pair is processed).  Every depth gives the same bits, for 1 and 8 blocks per trajectory."""
+    net = W.random_mass_action(n_species, 3000, seed=515, c_sigma=1.0)
+    x0 = W.poisson_x0(n_species, 40, 516)
+    o = oracle.run(net, x0, math.inf, 2, seed=4, max_events=300, want_grad=True, n_threads=2)
+    for C in (1, 8):
+        g = api.simulate(api.Network(net), x0, math.inf, 2, seed=4, max_events=300, grad=True,
+                         mapping=L.RT_MAP_BUNDLE, ctas_per_traj=C)
+        assert_same(g, o)
+
+
 def test_bundle_small_networks_and_edge_cases():
     """Networks smaller than a block, absorption and bad initial states in the bundle kernel."""
     for seed in range(3):
