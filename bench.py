@@ -40,6 +40,12 @@ SAMPLE_DT = 0.01
 # FP64 issue rate: nominal 1.25 TFLOP/s counts an FMA as 2 flops, so single adds,
 # multiplies, divides and conversions retire at most 0.625e12 per second.
 FP64_OP_PEAK = 0.625e12
+# DRAM bytes per unit of work of the roofline kernels, each from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch divided by the units it
+# processed; commands and figures in profiles/large_network_bundle_kernel.md and
+# profiles/ensemble_small_kernel_ncu.md).  Set to None when the kernel changes.
+NCU_BYTES_PER_CHANNEL_EVENT_BUNDLE = (77561792000 + 25620354048) / (200 * 16 * 1e6)
+NCU_BYTES_PER_TRAJECTORY_ENSEMBLE_LV = (830464 + 0) / 16384
 
 
 def parse():
@@ -226,7 +232,11 @@ def run_large(args):
                        "l2": "inputs larger than L2 (16 x 24 MB of P, T, a streamed per event)"},
             "clocks": clocks, "gpu_launches": 2 * len(evts),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "k_bundle",
+                         "frac": achieved / peak,
+                         "traffic": (NCU_BYTES_PER_CHANNEL_EVENT_BUNDLE * M * per_launch_events
+                                     if NCU_BYTES_PER_CHANNEL_EVENT_BUNDLE else None),
+                         "traffic_note": "ncu DRAM bytes of a 200-event launch, scaled to this launch's "
+                                         "channel-events", "kernel": "k_bundle",
                          "bytes_per_channel_event": 32, "peak_source": how}}
     if rank == 0:
         print(json.dumps(line))
@@ -511,7 +521,11 @@ def main():
             "clocks": clocks,
             "gpu_launches": len(evts),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_OP_PEAK / 1e12, "unit": "TFLOP/s",
-                         "frac": achieved * 1e12 / FP64_OP_PEAK, "traffic": None,
+                         "frac": achieved * 1e12 / FP64_OP_PEAK,
+                         "traffic": (NCU_BYTES_PER_TRAJECTORY_ENSEMBLE_LV * n
+                                     if NCU_BYTES_PER_TRAJECTORY_ENSEMBLE_LV else None),
+                         "traffic_note": "ncu DRAM bytes of a 16384-trajectory launch to t_end=10, scaled to "
+                                         "this launch's trajectories",
                          "kernel": "k_ens_small (Lotka-Volterra launch)", "launch_ms": lv_ms[-1],
                          "fp64_ops_per_event": ops / lv_events,
                          "peak_note": "FP64 pipe: nominal 1.25 TFLOP/s with FMA=2 -> 0.625e12 single ops/s (fallback)"},
