@@ -67,6 +67,26 @@ def parse():
     return ap.parse_args()
 
 
+def traj_base(rank: int, step: int, n: int) -> int:
+    """First global trajectory id of a rank's step: each (rank, step) pair owns its own block of
+    n ids (steps < 1000), so ranks and steps never repeat a trajectory (weak scaling, no
+    data-path collective)."""
+    return (rank * 1000 + step) * n
+
+
+def combine_over_ranks(ms: float, events: int, world: int, device=None):
+    """Whole-job time (the slowest rank) and events (summed over ranks) of a timed region."""
+    if world <= 1:
+        return ms, events
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([int(events)], dtype=torch.int64, device=device)
+    dist.all_reduce(e)
+    return t.item(), int(e.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -199,7 +219,7 @@ def run_large(args):
         if ev is not None:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-        o = api.simulate(netg, x0, math.inf, n_traj, seed=1, traj_offset=(rank * 1000 + i) * n_traj,
+        o = api.simulate(netg, x0, math.inf, n_traj, seed=1, traj_offset=traj_base(rank, i, n_traj),
                          max_events=args.events, mapping=L.RT_MAP_BUNDLE, outputs=outs)
         outs.update(o)
         if ev is not None:
@@ -415,7 +435,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     def step(i, timed_events=None):
-        base = (rank * 1000 + i) * n  # disjoint trajectory ids per step and rank
+        base = traj_base(rank, i, n)
         for k, c in enumerate(cfgs):
             for key in ("grid_sum", "grid_sumsq", "grid_count"):
                 outs[k][key].zero_()
@@ -449,12 +469,7 @@ def main():
     clocks = sampler.stop()
     per_launch = [(k, a.elapsed_time(b)) for k, a, b in evts]
     dev_ms = sum(ms for _, ms in per_launch)
-    if world > 1:
-        t = torch.tensor([dev_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ev_t = torch.tensor([float(total_events)], device=dev)
-        torch.distributed.all_reduce(ev_t)
-        dev_ms, total_events = t.item(), int(ev_t.item())
+    dev_ms, total_events = combine_over_ranks(dev_ms, total_events, world, dev)
     value = total_events / (dev_ms / 1e3)
 
     # dominant kernel: the Lotka-Volterra launch; its algorithmic FP64 ops from the firing counts
@@ -463,7 +478,7 @@ def main():
     netc = api.Network(cfgs[0]["net"])
     # firing mix of the last timed Lotka-Volterra launch from its first n/16 trajectories (same ids)
     chk = api.simulate(netc, x0s[0], args.t_end, max(1, n // 16), seed=1,
-                       traj_offset=(rank * 1000 + args.steps - 1) * n, grad=True, mapping=L.RT_MAP_THREAD,
+                       traj_offset=traj_base(rank, args.steps - 1, n), grad=True, mapping=L.RT_MAP_THREAD,
                        max_events=cfgs[0]["max_events"])
     counts = chk["counts"].sum(0, dtype=torch.int64).cpu().numpy()
     ops_s, ev_s = fp64_ops_per_event(cfgs[0]["net"], counts)
@@ -490,7 +505,7 @@ def main():
             xd = x0_host[k].to(dev, non_blocking=True)
             for key in ("grid_sum", "grid_sumsq", "grid_count"):
                 outs[k][key].zero_()
-            api.simulate(nets[k], xd, c["t_end"], n, seed=c["seed"], traj_offset=(rank * 1000 + 50 + i) * n,
+            api.simulate(nets[k], xd, c["t_end"], n, seed=c["seed"], traj_offset=traj_base(rank, 50 + i, n),
                          sample_dt=SAMPLE_DT, max_events=c["max_events"], grid="moments", mapping=L.RT_MAP_THREAD,
                          outputs=outs[k])
             for key, hv in host_out[k].items():
@@ -499,11 +514,9 @@ def main():
         b.synchronize()
         e2e_ms += a.elapsed_time(b)
         e2e_events += sum(int(ho["n_events"].sum()) for ho in host_out)
+    if e2e_ms > 0:
+        e2e_ms, e2e_events = combine_over_ranks(e2e_ms, e2e_events, world, dev)
     e2e_value = e2e_events / (e2e_ms / 1e3) if e2e_ms > 0 else None
-    if world > 1 and e2e_ms > 0:
-        t = torch.tensor([e2e_ms, float(e2e_events)], device=dev)
-        torch.distributed.all_reduce(t)  # events summed; time summed then divided below
-        e2e_value = t[1].item() / (t[0].item() / world / 1e3)
 
     if rank == 0:
         line = {
