@@ -69,3 +69,25 @@ def test_batch_graph_capture_replays_identically():
     for k in out:
         assert torch.equal(out[k], first[k])
     check_against_oracle(items, batch, out, 2, 2500, 4)
+
+
+def test_full_size_batch_sampled_against_oracle():
+    """The benchmarked batch: 4096 networks, M ~ U{4..4096}, one trajectory each, 20000-event cap,
+    in one graph-captured launch; 12 networks spread over the batch (the largest included) are
+    re-run one by one in the oracle."""
+    items = W.batched_networks(4096)
+    batch = api.Batch([it.net for it in items])
+    x0 = torch.from_numpy(np.concatenate([it.x0 for it in items])).cuda()
+    t_end = torch.tensor([it.t_end for it in items], dtype=torch.float64).cuda()
+    graph, out = batch.capture(x0, t_end, 1, seed=1, max_events=20000)
+    graph.replay()
+    torch.cuda.synchronize()
+    ms = np.array([it.net.n_reactions for it in items])
+    picks = sorted(set(np.linspace(0, 4095, 11).astype(int).tolist() + [int(ms.argmax())]))
+    for i in picks:
+        it = items[i]
+        o = oracle.run(it.net, it.x0, it.t_end, 1, seed=1, stream_id=i, max_events=20000, n_threads=1)
+        assert np.array_equal(batch.x_final_of(out, i, 1).cpu().numpy(), o["x_final"]), i
+        assert np.array_equal(out["n_events"][i].cpu().numpy(), o["n_events"]), i
+        assert np.array_equal(out["status"][i].cpu().numpy(), o["status"]), i
+        assert np.array_equal(out["t_last"][i].cpu().numpy().view(np.int64), o["t_last"].view(np.int64)), i
