@@ -63,6 +63,7 @@ def parse():
                     help="ensemble (default): LV + birth-death + dimerisation; large: N=1e4, M=1e6, 16 trajectories; "
                          "batched: 4096 uneven networks in one persistent launch; grad: M=64 forward + backward")
     ap.add_argument("--batch-events", type=int, default=20_000, help="batched workload: event cap per network")
+    ap.add_argument("--nets", type=int, default=4096, help="batched workload: networks (reduced only for captures)")
     ap.add_argument("--events", type=int, default=100_000, help="large workload: events per trajectory per step")
     return ap.parse_args()
 
@@ -289,7 +290,7 @@ def run_batched(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    items = W.batched_networks(4096)
+    items = W.batched_networks(args.nets)
     specs = [it.net for it in items]
     x0 = torch.from_numpy(np.concatenate([it.x0 for it in items])).to(dev)
     t_end = torch.tensor([it.t_end for it in items], dtype=torch.float64, device=dev)
@@ -334,8 +335,9 @@ def run_batched(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "batched: 4096 random networks, M~U{4..4096}, N=M/4, c~lognormal(0,1), "
-                                   "X0~Poisson(50), t_end~U[1,10], 1 trajectory each, one persistent graph launch",
+            "config": {"workload": "batched: %d random networks, M~U{4..4096}, N=M/4, c~lognormal(0,1), "
+                                   "X0~Poisson(50), t_end~U[1,10], 1 trajectory each, one persistent graph launch"
+                                   % args.nets,
                        "max_events_per_network": cap, "policy": policy, "events_per_step": events},
             "clocks": clocks, "gpu_launches": len(ms),
             "subset_512": {"batched_events_per_s": sub_events / (statistics.mean(ms_sub) / 1e3),
