@@ -192,7 +192,7 @@ def batched_networks(n_nets: int = 4096, m_lo: int = 4, m_hi: int = 4096, seed: 
 
 
 # --------------------------------------------------------------------------------------
-# The five workloads of the evaluation (sizes as published for this build).
+# The five evaluation workloads at their benchmarked sizes.
 # --------------------------------------------------------------------------------------
 
 def lv_config(n_traj: int = 64):
