@@ -163,27 +163,38 @@ def cpu_baseline(cfgs, sample):
         ev += int(o["n_events"].sum())
     dt = time.perf_counter() - t0
     return {"value": ev / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "%d trajectories of each of the 3 networks to t_end=10 (%d events, %.1f s)" % (sample, ev, dt)}
+            "sample": "%d trajectories of each of the 3 networks to t_end=%g (%d events, %.1f s)"
+                      % (sample, cfgs[0]["t_end"], ev, dt)}
+
+
+ENSEMBLE_WORKLOAD = ("ensemble: Lotka-Volterra (Table 4, X0=Y0=1000) + birth-death (k=100, gamma=1) "
+                     "+ dimerisation (0.001/0.1, A0=1000), 2^20 trajectories each, t_end=10, "
+                     "one thread per trajectory")
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle on the host cores, on the ensemble workload's metric and
+    config, each step a bounded sample of it (--cpu-sample trajectories of each network)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     cfgs = W.ensemble_configs(args.traj)
     sample = args.cpu_sample
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state
-    vals, times = [], []
+    for _ in range(args.warmup):  # untimed: loads the oracle and pages its code in
+        cpu_baseline(cfgs, 8)
+    vals, secs = [], []
     for _ in range(args.steps):
+        t0 = time.perf_counter()
         b = cpu_baseline(cfgs, sample)
+        secs.append(time.perf_counter() - t0)
         vals.append(b["value"])
     b["value"] = statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "ensemble: Lotka-Volterra + birth-death + dimerisation, CPU oracle sample",
-                       "trajectories_per_network": sample, "t_end": 10.0, "seed": 1},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": ENSEMBLE_WORKLOAD, "trajectories_per_network": args.traj, "t_end": args.t_end,
+                       "sample_dt": SAMPLE_DT, "seed": 1, "max_events_per_trajectory": cfgs[0]["max_events"],
+                       "parallelism": "host cores"},
             "cpu_baseline": b, "e2e": {"value": b["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                                        "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -525,9 +536,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "ensemble: Lotka-Volterra (Table 4, X0=Y0=1000) + birth-death (k=100, gamma=1) "
-                                   "+ dimerisation (0.001/0.1, A0=1000), 2^20 trajectories each, t_end=10, "
-                                   "one thread per trajectory",
+            "config": {"workload": ENSEMBLE_WORKLOAD,
                        "trajectories_per_network": n, "t_end": args.t_end, "sample_dt": SAMPLE_DT, "seed": 1,
                        "max_events_per_trajectory": cfgs[0]["max_events"],
                        "parallelism": "trajectories sharded over ranks" if world > 1 else "1 GPU",
