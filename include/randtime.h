@@ -60,7 +60,8 @@ enum {
 /* Trajectory-to-hardware mappings. */
 enum {
   RT_MAP_AUTO = -1,  /* chosen by the library from the network size */
-  RT_MAP_THREAD = 0, /* one thread per trajectory, state in registers (small M) */
+  RT_MAP_THREAD = 0, /* one thread per trajectory, state in registers (M <= 16; with M <= 4 and
+                        N <= 4 the counts and the network too) */
   RT_MAP_WARP = 1,   /* one warp per trajectory, channels spread over lanes */
   RT_MAP_BLOCK = 2,  /* one thread block per trajectory, state in registers (M <= 8 * block_threads) */
   RT_MAP_BUNDLE = 3  /* several blocks per trajectory, state streamed through HBM */
