@@ -105,3 +105,32 @@ def test_block_mapping_finite_horizon_likelihood():
     o = oracle.run(net, x0, 0.01, 9, seed=3, want_grad=True, max_events=100000, n_threads=9)
     assert (o["status"] == 0).all()
     assert_same(g, o)
+
+
+def _overflow_network(M):
+    """M - 1 slow first-order conversions among species 1..3 and one fast birth of species 0."""
+    rng = np.random.default_rng(M)
+    reactions = []
+    for _ in range(M - 1):
+        a, b = rng.choice([1, 2, 3], size=2, replace=False)
+        reactions.append(({int(a): 1}, {int(b): 1}, float(rng.uniform(0.5, 2.0))))
+    reactions.append(({}, {0: 1}, 1e6))
+    return W._from_lists(4, reactions, "overflow%d" % M)
+
+
+@pytest.mark.parametrize("grid", [False, True])
+@pytest.mark.parametrize("mapping,M", [(L.RT_MAP_WARP, 100), (L.RT_MAP_BLOCK, 700), (L.RT_MAP_BUNDLE, 700)])
+def test_overflow_stops_before_the_event(mapping, M, grid):
+    """A fast birth drives species 0 to INT32_MAX: the event that would pass it does not fire and
+    the run stops with OVERFLOW, with the grid (sampled densely, so the last events cross grid
+    points) and the counts as the oracle has them."""
+    net = _overflow_network(M)
+    x0 = np.array([[2**31 - 60, 50, 50, 50], [2**31 - 7, 10, 10, 10], [5, 50, 50, 50]], np.int32)
+    kw = dict(grid="traj", sample_dt=2e-6) if grid else {}
+    g = api.simulate(api.Network(net), x0, 1e-3, 3, seed=6, grad=True, mapping=mapping,
+                     ctas_per_traj=2 if mapping == L.RT_MAP_BUNDLE else 0, **kw)
+    o = oracle.run(net, x0, 1e-3, 3, seed=6, want_grad=True, want_grid=grid, n_threads=3,
+                   **({"sample_dt": 2e-6} if grid else {}))
+    assert o["status"][:2].tolist() == [oracle.ST_OVERFLOW, oracle.ST_OVERFLOW]
+    assert o["status"][2] == oracle.ST_TEND
+    assert_same(g, o)
