@@ -177,9 +177,10 @@ __device__ __forceinline__ void simulate_small(const RunArgs &A, const SmallNet 
       ++ev;
       // Eq. 27: only the fired channel draws a new increment
       const double E = exp1_draw(A.seed, g, (uint32_t)mu, (uint32_t)nmu, A.stream_id);
+      const double Pmu = __dadd_rn(pick<MAXM>(P, mu), E);  // one FP64 add, placed by selects
 #pragma unroll
       for (int k = 0; k < MAXM; ++k) {
-        if (k == mu) P[k] = __dadd_rn(P[k], E);
+        if (k == mu) P[k] = Pmu;
         if ((dm >> k) & 1u) a[k] = propensity(make_int2(SN.s0[k], SN.s1[k]), SN.c[k], xat);
       }
     }
