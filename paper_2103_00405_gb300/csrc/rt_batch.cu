@@ -287,9 +287,10 @@ extern "C" int rt_batch_create(int32_t n_nets, const rt_network *const *nets, co
   const size_t s_thread = (size_t)BT * b->maxN_thread * 4;
   b->smem = std::max({s_block, s_warp, s_thread, (size_t)16});
   if (b->smem > 200 * 1024) {
+    const size_t need = b->smem;
     cudaFree(b->arena);
     delete b;
-    return set_error(RT_ERR_UNSUPPORTED, "batch networks need %zu bytes of shared memory", b->smem);
+    return set_error(RT_ERR_UNSUPPORTED, "batch networks need %zu bytes of shared memory", need);
   }
   if (b->smem > 48 * 1024) cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
   int per_sm = 0, sms = 0;
