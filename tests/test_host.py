@@ -111,3 +111,17 @@ def test_lotka_volterra_is_table_4_model():
     assert net.dense_reactants().tolist() == [[1, 0], [1, 1], [0, 1]]
     assert net.dense_stoich().tolist() == [[1, 0], [-1, 1], [0, -1]]
     assert net.c.tolist() == [10.0, 0.01, 10.0]
+
+
+def test_large_network_config_shape_and_realised_dependency_degree():
+    """N = 1e4, M = 1e6 with uniform reactants: ~150 reading reactions per species and a dependency
+    out-degree of a few hundred per reaction (the recomputes per event of the large-network scan)."""
+    net = W.large_network_config()["net"]
+    N, M = net.n_species, net.n_reactions
+    assert (N, M) == (10_000, 1_000_000)
+    pairs = np.unique(np.stack([net.reac_rxn, net.reac_sp], 1), axis=0)
+    readers = np.bincount(pairs[:, 1], minlength=N)
+    assert 140 < readers.mean() < 160
+    changed = net.stoi_delta != 0
+    deg = np.bincount(net.stoi_rxn[changed], weights=readers[net.stoi_sp[changed]], minlength=M)
+    assert 300 < deg.mean() < 450
