@@ -104,6 +104,11 @@ typedef struct rt_outputs {
   double *loglik_dev;      /* [n_traj] path log-likelihood sum ln a_mu - sum_k T_k(t_end) */
   int32_t *counts_dev;     /* [n_traj][M] firings n_k per channel */
   double *t_internal_dev;  /* [n_traj][M] internal times T_k(t_end) */
+  int64_t trace_len;       /* events recorded per trajectory in trace_*_dev (0: no trace) */
+  int32_t *trace_mu_dev;   /* [n_traj][trace_len] channel fired by event e (Table 2's triggered j);
+                              -1 after the trajectory's last event */
+  double *trace_t_dev;     /* [n_traj][trace_len] time t of event e (after the update t += dt);
+                              0 after the trajectory's last event */
 } rt_outputs;
 
 /*
@@ -186,9 +191,11 @@ int rt_run(const rt_network *net, const rt_run_params *params, const rt_outputs 
  * lives in a fixed 16 MiB device array inside the library, which every GPU that
  * loads the library holds until the process exits; a run that needs more (about
  * 28 bytes per channel per trajectory plus a few KB) returns RT_ERR_OOM with a
- * message, and nothing is enqueued.  The first call on a device looks up that
- * array's device address (once per device, with the device current); make that
- * first call before any stream capture.  All calls on a device share the array
+ * message, and nothing is enqueued.  Every call looks up that array's device
+ * address on the current device (cudaGetSymbolAddress, which allocates nothing), so
+ * a device reset between calls is harmless; the first call on a device loads the
+ * library's device code there, so make it before any stream capture.  All calls on
+ * a device share the array
  * and it keeps the last call's contents: calls whose work overlaps on the GPU
  * (different streams, or threads without ordering) race on it, so order them on
  * one stream or synchronise between them.
@@ -239,8 +246,8 @@ int rt_philox(int64_t count, const uint32_t *ctr_dev, uint32_t key0, uint32_t ke
  * block_threads).  Work is a list of block-sized tasks (one block-class
  * trajectory, block_threads/32 warp-class or block_threads thread-class
  * trajectories), larger networks first, that persistent blocks take from an
- * atomic counter.  Network i draws its random numbers with stream_id = i, so its
- * trajectories equal rt_run of that network with stream_id = i.
+ * atomic counter.  Network i draws its random numbers with its own stream id
+ * (default i), so its trajectories equal rt_run of that network with that stream id.
  */
 typedef struct rt_batch_policy {
   int32_t thread_max_m;  /* <= 8; networks with more than 8 species go to the warp class */
@@ -250,10 +257,15 @@ typedef struct rt_batch_policy {
 } rt_batch_policy;
 
 /* Pack the networks into one device arena (the batch keeps its own copy; the
- * network handles may be destroyed afterwards).  policy may be NULL (defaults 8 / 256 / 512 / 0).  All
- * networks must live on the current device.  Networks too large for the block
- * class (M > 8 * block_threads) return RT_ERR_UNSUPPORTED. */
-int rt_batch_create(int32_t n_nets, const rt_network *const *nets, const rt_batch_policy *policy, rt_batch **out);
+ * network handles may be destroyed afterwards).  stream_ids: host array [n_nets],
+ * the Philox stream (fourth counter word) of each network's draws, or NULL for
+ * network i -> stream i; a run sharded over several GPUs passes each network's
+ * global index so its trajectories equal the single-GPU run's.  policy may be NULL
+ * (defaults 8 / 256 / 512 / 0).  All networks must live on the current device.
+ * Networks too large for the block class (M > 8 * block_threads) return
+ * RT_ERR_UNSUPPORTED. */
+int rt_batch_create(int32_t n_nets, const rt_network *const *nets, const uint32_t *stream_ids,
+                    const rt_batch_policy *policy, rt_batch **out);
 void rt_batch_destroy(rt_batch *batch);
 
 /* Totals of the packed batch: species (length of packed x0), reactions, and the
@@ -261,19 +273,48 @@ void rt_batch_destroy(rt_batch *batch);
 int rt_batch_info(const rt_batch *batch, int64_t *total_species, int64_t *total_reactions, int32_t *n_thread_class,
                   int32_t *n_warp_class, int32_t *n_block_class);
 
+/* Where a batched run's results go.  Any pointer may be NULL (output not produced).
+ * Network i has N_i species and M_i reactions; "packed" arrays hold network after
+ * network, each as [traj j][N_i] or [traj j][M_i] (the offsets are n_traj times the
+ * sums of N or M over the networks before i). */
+typedef struct rt_batch_outputs {
+  int32_t *x_final_dev;    /* packed [net i][traj j][N_i] final states */
+  int64_t *n_events_dev;   /* [n_nets][n_traj] events fired */
+  int32_t *status_dev;     /* [n_nets][n_traj] RT_TRAJ_* */
+  double *t_last_dev;      /* [n_nets][n_traj] time of the last fired event */
+  double *loglik_dev;      /* [n_nets][n_traj] path log-likelihood, as rt_outputs.loglik_dev */
+  int32_t *counts_dev;     /* packed [net i][traj j][M_i] firings n_k */
+  double *t_internal_dev;  /* packed [net i][traj j][M_i] internal times T_k(t_end) */
+  int64_t trace_len;       /* events recorded per trajectory (0: none) */
+  int32_t *trace_mu_dev;   /* [n_nets][n_traj][trace_len] fired channels, -1 after the last event */
+  double *trace_t_dev;     /* [n_nets][n_traj][trace_len] event times, 0 after the last event */
+} rt_batch_outputs;
+
 /*
  * rt_batch_run -- n_traj_per_net trajectories of every network, in one launch
  * (plus a counter reset), enqueued on `stream` without host synchronisation, so
  * it can be captured in a CUDA graph.
  *   x0_dev:    initial counts, network after network (sum of N_i int32)
  *   t_end_dev: [n_nets] horizons (finite, >= 0)
- *   outputs (any may be NULL): x_final_dev packed as [net i][traj j][N_i];
- *   n_events_dev, status_dev, t_last_dev as [net i][traj j].
- * max_events caps every trajectory (0 <= max_events <= INT32_MAX).
+ *   outputs:   rt_batch_outputs (NULL: nothing written)
+ * max_events caps every trajectory (0 <= max_events <= INT32_MAX).  Network i's
+ * trajectory j equals rt_run of that network with stream_id = its stream id and
+ * traj_offset = 0 (trajectory j), bit for bit.
  */
 int rt_batch_run(rt_batch *batch, const int32_t *x0_dev, const double *t_end_dev, int64_t max_events,
-                 uint64_t seed, int64_t n_traj_per_net, int32_t *x_final_dev, int64_t *n_events_dev,
-                 int32_t *status_dev, double *t_last_dev, void *stream);
+                 uint64_t seed, int64_t n_traj_per_net, const rt_batch_outputs *outputs, void *stream);
+
+/*
+ * rt_fp64_probe -- a measurement aid with no counterpart in the paper: launches
+ * blocks_per_sm x (number of SMs) blocks of 256 threads, each thread running 8
+ * independent chains of `iters` binary64 multiply-then-add steps (never fused),
+ * so that the time of the launch (taken by the caller with CUDA events on
+ * `stream`) gives the GPU's binary64 add/multiply issue rate.  *ops (host
+ * pointer, may be NULL) receives the number of binary64 operations the launch
+ * performs.  sink_dev: one device double, written only in a case that never
+ * happens (it keeps the loop from being optimised away).
+ */
+int rt_fp64_probe(int64_t iters, int32_t blocks_per_sm, double *sink_dev, double *ops, void *stream);
 
 /* Message describing the last error on this host thread ("" if none). */
 const char *rt_last_error(void);

@@ -37,7 +37,14 @@ class rt_batch_policy(ctypes.Structure):
 class rt_outputs(ctypes.Structure):
     _fields_ = [("x_final_dev", vp), ("grid_dev", vp), ("grid_sum_dev", vp), ("grid_sumsq_dev", vp),
                 ("grid_count_dev", vp), ("n_events_dev", vp), ("status_dev", vp), ("t_last_dev", vp),
-                ("loglik_dev", vp), ("counts_dev", vp), ("t_internal_dev", vp)]
+                ("loglik_dev", vp), ("counts_dev", vp), ("t_internal_dev", vp), ("trace_len", i64),
+                ("trace_mu_dev", vp), ("trace_t_dev", vp)]
+
+
+class rt_batch_outputs(ctypes.Structure):
+    _fields_ = [("x_final_dev", vp), ("n_events_dev", vp), ("status_dev", vp), ("t_last_dev", vp),
+                ("loglik_dev", vp), ("counts_dev", vp), ("t_internal_dev", vp), ("trace_len", i64),
+                ("trace_mu_dev", vp), ("trace_t_dev", vp)]
 
 
 # (name, restype, argtypes) of every entry point declared in include/randtime.h
@@ -56,10 +63,11 @@ SIGNATURES = [
     ("rt_draw_exp1", ctypes.c_int, [u64, u32, i64, vp, vp, vp, vp, vp, vp]),
     ("rt_log_eval", ctypes.c_int, [i64, vp, vp, vp]),
     ("rt_philox", ctypes.c_int, [i64, vp, u32, u32, vp, vp]),
-    ("rt_batch_create", ctypes.c_int, [i32, vp, ctypes.POINTER(rt_batch_policy), ctypes.POINTER(vp)]),
+    ("rt_batch_create", ctypes.c_int, [i32, vp, vp, ctypes.POINTER(rt_batch_policy), ctypes.POINTER(vp)]),
     ("rt_batch_destroy", None, [vp]),
     ("rt_batch_info", ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
-    ("rt_batch_run", ctypes.c_int, [vp, vp, vp, i64, u64, i64, vp, vp, vp, vp, vp]),
+    ("rt_batch_run", ctypes.c_int, [vp, vp, vp, i64, u64, i64, ctypes.POINTER(rt_batch_outputs), vp]),
+    ("rt_fp64_probe", ctypes.c_int, [i64, i32, vp, ctypes.POINTER(dbl), vp]),
     ("rt_last_error", ctypes.c_char_p, []),
 ]
 

@@ -78,13 +78,15 @@ def grid_len(t_end: float, sample_dt: float) -> int:
 def simulate(net: Network, x0, t_end: float, n_traj: int, seed: int = 1, stream_id: int = 0,
              traj_offset: int = 0, max_events: int = (1 << 31) - 1, sample_dt: float = 0.0,
              grid: str = "none", grad: bool = False, mapping: Optional[int] = None, block_threads: int = 0,
-             ctas_per_traj: int = 0, outputs: Optional[dict] = None) -> dict:
+             ctas_per_traj: int = 0, trace_len: int = 0, outputs: Optional[dict] = None) -> dict:
     """Simulate n_traj trajectories; returns a dict of CUDA tensors.
 
     x0: [N] or [n_traj, N] int32 (numpy, list or tensor; copied to the device if needed).
     grid: "none", "traj" (per-trajectory [n_traj, G, N]) or "moments" (sums over
     trajectories of X and X^2 per grid point, plus counts).
     grad: also return loglik [n_traj], counts [n_traj, M], t_internal [n_traj, M].
+    trace_len: also return trace_mu [n_traj, trace_len] (fired channel of each of the first
+    trace_len events, -1 after the last) and trace_t (event times, 0 after the last).
     outputs: optional dict of preallocated tensors (same keys) to write into; missing entries are
     allocated and added to it.
     """
@@ -123,6 +125,11 @@ def simulate(net: Network, x0, t_end: float, n_traj: int, seed: int = 1, stream_
         o.loglik_dev = _ptr(get("loglik", (n_traj,), torch.float64))
         o.counts_dev = _ptr(get("counts", (n_traj, M), torch.int32))
         o.t_internal_dev = _ptr(get("t_internal", (n_traj, M), torch.float64))
+
+    if trace_len:
+        o.trace_len = int(trace_len)
+        o.trace_mu_dev = _ptr(get("trace_mu", (n_traj, int(trace_len)), torch.int32))
+        o.trace_t_dev = _ptr(get("trace_t", (n_traj, int(trace_len)), torch.float64))
 
     p = L.rt_run_params(_ptr(x0t), per, int(stream_id), float(t_end), int(max_events), int(seed) & (2**64 - 1),
                         int(n_traj), int(traj_offset), float(sample_dt))
@@ -178,19 +185,26 @@ class LogLik(torch.autograd.Function):
 class Batch:
     """Many networks in one persistent launch (rt_batch_create / rt_batch_run).
 
-    Network i draws its random numbers with stream_id = i, so its trajectories are
-    those of ``simulate(Network(specs[i]), ..., stream_id=i)``.
+    Network i draws its random numbers with stream_id = stream_ids[i] (default i), so its
+    trajectories are those of ``simulate(Network(specs[i]), ..., stream_id=stream_ids[i])``.
     """
 
     def __init__(self, specs, thread_max_m: int = 8, warp_max_m: int = 256, block_threads: int = 512,
-                 blocks_per_sm: int = 0):
+                 blocks_per_sm: int = 0, stream_ids=None):
         self.lib = L.load()
         nets = [Network(s) for s in specs]
         arr = (ctypes.c_void_p * len(nets))(*[n.handle.value for n in nets])
         pol = L.rt_batch_policy(thread_max_m, warp_max_m, block_threads, blocks_per_sm)
         h = ctypes.c_void_p()
-        L.check(self.lib.rt_batch_create(len(nets), ctypes.cast(arr, ctypes.c_void_p), ctypes.byref(pol),
-                                         ctypes.byref(h)), "rt_batch_create")
+        sid = None
+        if stream_ids is not None:
+            sid = np.ascontiguousarray(stream_ids, dtype=np.uint32)
+            if sid.shape != (len(nets),):
+                raise ValueError("stream_ids must have one entry per network")
+        self.stream_ids = sid if sid is not None else np.arange(len(nets), dtype=np.uint32)
+        L.check(self.lib.rt_batch_create(len(nets), ctypes.cast(arr, ctypes.c_void_p),
+                                         None if sid is None else sid.ctypes.data_as(ctypes.c_void_p),
+                                         ctypes.byref(pol), ctypes.byref(h)), "rt_batch_create")
         for n in nets:  # the batch keeps its own copy
             n.close()
         self.handle = h
@@ -198,6 +212,7 @@ class Batch:
         self.N = np.array([s.n_species for s in specs], np.int64)
         self.M = np.array([s.n_reactions for s in specs], np.int64)
         self.xoff = np.concatenate([[0], np.cumsum(self.N)[:-1]])
+        self.moff = np.concatenate([[0], np.cumsum(self.M)[:-1]])
         self.policy = (thread_max_m, warp_max_m, block_threads, blocks_per_sm)
 
     def info(self):
@@ -208,21 +223,43 @@ class Batch:
         return dict(total_species=ts.value, total_reactions=tr.value, n_thread=c[0].value, n_warp=c[1].value,
                     n_block=c[2].value)
 
-    def outputs(self, n_traj: int):
+    def outputs(self, n_traj: int, grad: bool = False, trace_len: int = 0):
+        """Device tensors for a run: x_final packed [net i][traj j][N_i]; n_events, status, t_last
+        [n_nets, n_traj]; with grad also loglik [n_nets, n_traj] and counts / t_internal packed
+        [net i][traj j][M_i]; with trace_len also trace_mu / trace_t [n_nets, n_traj, trace_len]."""
         dev = torch.device("cuda", torch.cuda.current_device())
         n = len(self.specs)
-        return dict(x_final=torch.empty(int(self.N.sum()) * n_traj, dtype=torch.int32, device=dev),
-                    n_events=torch.empty((n, n_traj), dtype=torch.int64, device=dev),
-                    status=torch.empty((n, n_traj), dtype=torch.int32, device=dev),
-                    t_last=torch.empty((n, n_traj), dtype=torch.float64, device=dev))
+        out = dict(x_final=torch.empty(int(self.N.sum()) * n_traj, dtype=torch.int32, device=dev),
+                   n_events=torch.empty((n, n_traj), dtype=torch.int64, device=dev),
+                   status=torch.empty((n, n_traj), dtype=torch.int32, device=dev),
+                   t_last=torch.empty((n, n_traj), dtype=torch.float64, device=dev))
+        if grad:
+            out["loglik"] = torch.empty((n, n_traj), dtype=torch.float64, device=dev)
+            out["counts"] = torch.empty(int(self.M.sum()) * n_traj, dtype=torch.int32, device=dev)
+            out["t_internal"] = torch.empty(int(self.M.sum()) * n_traj, dtype=torch.float64, device=dev)
+        if trace_len:
+            out["trace_mu"] = torch.empty((n, n_traj, int(trace_len)), dtype=torch.int32, device=dev)
+            out["trace_t"] = torch.empty((n, n_traj, int(trace_len)), dtype=torch.float64, device=dev)
+        return out
 
     def run(self, x0: torch.Tensor, t_end: torch.Tensor, n_traj: int, seed: int = 1,
             max_events: int = (1 << 31) - 1, outputs: Optional[dict] = None) -> dict:
         """x0: packed int32 device tensor (sum of N_i); t_end: float64 device tensor [n_nets]."""
         out = outputs if outputs is not None else self.outputs(n_traj)
+        o = L.rt_batch_outputs()
+        o.x_final_dev = _ptr(out.get("x_final"))
+        o.n_events_dev = _ptr(out.get("n_events"))
+        o.status_dev = _ptr(out.get("status"))
+        o.t_last_dev = _ptr(out.get("t_last"))
+        o.loglik_dev = _ptr(out.get("loglik"))
+        o.counts_dev = _ptr(out.get("counts"))
+        o.t_internal_dev = _ptr(out.get("t_internal"))
+        if "trace_mu" in out:
+            o.trace_len = int(out["trace_mu"].shape[2])
+            o.trace_mu_dev = _ptr(out["trace_mu"])
+            o.trace_t_dev = _ptr(out.get("trace_t"))
         L.check(self.lib.rt_batch_run(self.handle, _ptr(x0), _ptr(t_end), int(max_events), int(seed) & (2**64 - 1),
-                                      int(n_traj), _ptr(out["x_final"]), _ptr(out["n_events"]), _ptr(out["status"]),
-                                      _ptr(out["t_last"]), _stream()), "rt_batch_run")
+                                      int(n_traj), ctypes.byref(o), _stream()), "rt_batch_run")
         return out
 
     def x_final_of(self, out: dict, i: int, n_traj: int) -> torch.Tensor:
@@ -230,10 +267,15 @@ class Batch:
         b = int(self.xoff[i]) * n_traj
         return out["x_final"][b:b + n_traj * int(self.N[i])].view(n_traj, int(self.N[i]))
 
+    def per_channel_of(self, out: dict, key: str, i: int, n_traj: int) -> torch.Tensor:
+        """[n_traj, M_i] counts or t_internal of network i from the packed output."""
+        b = int(self.moff[i]) * n_traj
+        return out[key][b:b + n_traj * int(self.M[i])].view(n_traj, int(self.M[i]))
+
     def capture(self, x0: torch.Tensor, t_end: torch.Tensor, n_traj: int, seed: int = 1,
-                max_events: int = (1 << 31) - 1):
+                max_events: int = (1 << 31) - 1, grad: bool = False, trace_len: int = 0):
         """Capture one rt_batch_run in a CUDA graph; returns (graph, outputs).  graph.replay() reruns it."""
-        out = self.outputs(n_traj)
+        out = self.outputs(n_traj, grad=grad, trace_len=trace_len)
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
@@ -285,3 +327,25 @@ def philox(ctr: torch.Tensor, key0: int, key1: int) -> torch.Tensor:
     out = torch.empty_like(c)
     L.check(lib.rt_philox(c.numel() // 4, _ptr(c), int(key0), int(key1), _ptr(out), _stream()), "rt_philox")
     return out
+
+
+def fp64_probe(iters: int = 4096, blocks_per_sm: int = 8, repeats: int = 3):
+    """Measured binary64 add/multiply issue rate (operations per second) of the current GPU:
+    the best of `repeats` timed rt_fp64_probe launches (CUDA events on the current stream)."""
+    lib = L.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sink = torch.zeros(1, dtype=torch.float64, device=dev)
+    ops = ctypes.c_double(0.0)
+    stream = torch.cuda.current_stream()
+    L.check(lib.rt_fp64_probe(int(iters), int(blocks_per_sm), _ptr(sink), ctypes.byref(ops), _stream()),
+            "rt_fp64_probe")  # warm-up
+    best = 0.0
+    for _ in range(repeats):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        L.check(lib.rt_fp64_probe(int(iters), int(blocks_per_sm), _ptr(sink), ctypes.byref(ops), _stream()),
+                "rt_fp64_probe")
+        b.record(stream)
+        b.synchronize()
+        best = max(best, ops.value / (a.elapsed_time(b) / 1e3))
+    return best

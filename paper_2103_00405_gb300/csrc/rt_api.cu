@@ -39,6 +39,7 @@ int validate_run(const rt_network *net, const rt_run_params *p, const rt_outputs
   if (want_grid && !std::isfinite(p->t_end)) return set_error(RT_ERR_INVALID_ARG, "grid outputs need a finite t_end");
   if ((o->grid_sumsq_dev || o->grid_count_dev) && !o->grid_sum_dev)
     return set_error(RT_ERR_INVALID_ARG, "grid_sumsq/grid_count need grid_sum");
+  if (o->trace_len < 0) return set_error(RT_ERR_INVALID_ARG, "trace_len must be >= 0");
   return RT_OK;
 }
 
@@ -205,4 +206,44 @@ extern "C" int rt_loglik_backward(const rt_network *net, int64_t n_traj, const d
                                                                      grad_c);
   const cudaError_t err = cudaGetLastError();
   return err == cudaSuccess ? RT_OK : set_error(RT_ERR_CUDA, "%s", cudaGetErrorString(err));
+}
+
+// ---------------------------------------------------------------------------
+// Measurement aid: the binary64 add/multiply issue rate of this GPU.  Each thread
+// runs kProbeChains independent chains x <- x * m + c (one DMUL and one DADD, never
+// fused: the library is built with --fmad=false and the intrinsics round each op),
+// so the FP64 pipe, not latency, bounds the loop.  The result is written only if
+// it equals an impossible value, which keeps the loop alive without memory traffic.
+// ---------------------------------------------------------------------------
+constexpr int kProbeChains = 8;
+constexpr int kProbeThreads = 256;
+
+__global__ void __launch_bounds__(kProbeThreads) k_fp64_probe(int64_t iters, double *sink) {
+  double x[kProbeChains];
+#pragma unroll
+  for (int i = 0; i < kProbeChains; ++i) x[i] = 1.0 + 1e-3 * (threadIdx.x + i);
+  const double m = 0.9999999, c = 1e-9;
+  for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < kProbeChains; ++i) x[i] = __dadd_rn(__dmul_rn(x[i], m), c);
+  }
+  double acc = 0.0;
+#pragma unroll
+  for (int i = 0; i < kProbeChains; ++i) acc = __dadd_rn(acc, x[i]);
+  if (acc == -1.0) sink[0] = acc;
+}
+
+extern "C" int rt_fp64_probe(int64_t iters, int32_t blocks_per_sm, double *sink_dev, double *ops, void *stream) {
+  clear_error();
+  if (iters < 1 || blocks_per_sm < 1 || blocks_per_sm > 64) return set_error(RT_ERR_INVALID_ARG, "iters >= 1, 1 <= blocks_per_sm <= 64");
+  if (!sink_dev) return set_error(RT_ERR_INVALID_ARG, "sink_dev is NULL");
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t grid = (int64_t)sms * blocks_per_sm;
+  k_fp64_probe<<<(unsigned)grid, kProbeThreads, 0, (cudaStream_t)stream>>>(iters, sink_dev);
+  const cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return set_error(RT_ERR_CUDA, "%s", cudaGetErrorString(err));
+  if (ops) *ops = 2.0 * kProbeChains * (double)kProbeThreads * (double)grid * (double)iters;
+  return RT_OK;
 }

@@ -9,7 +9,8 @@
 // block_threads thread-class trajectories.  Persistent blocks take tasks from an
 // atomic counter and run the same per-trajectory routines as the single-network
 // kernels (rt_traj_*.cuh), reading the network tables through generic pointers
-// into the arena.  Network i uses Philox stream i (the fourth counter word).
+// into the arena.  Network i uses its own Philox stream (the fourth counter word;
+// by default i).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,8 +30,11 @@ enum { CLS_THREAD = 0, CLS_WARP = 1, CLS_BLOCK = 2 };
 struct BNet {
   DevNet d;
   int64_t xoff;  // first species of this network in the packed x0 / x_final rows
+  int64_t moff;  // first reaction of this network in the packed counts / t_internal rows
   int32_t cls;
   int32_t R;     // register slots (warp and block: 1, 2, 4 or 8)
+  uint32_t stream_id;
+  int32_t pad;
 };
 
 struct BatchArgs {
@@ -45,10 +49,7 @@ struct BatchArgs {
   const double *t_end;
   int32_t max_events;
   uint64_t seed;
-  int32_t *x_final;
-  int64_t *n_events;
-  int32_t *status;
-  double *t_last;
+  rt_batch_outputs out;
   int maxN_thread, maxN_warp, maxM_block, maxN_block;
 };
 
@@ -57,7 +58,7 @@ __device__ __forceinline__ RunArgs item_args(const BatchArgs &B, int net_index, 
   A.net = bn.d;
   A.x0 = B.x0 + bn.xoff;
   A.per_traj_x0 = 0;
-  A.stream_id = (uint32_t)net_index;
+  A.stream_id = bn.stream_id;
   A.t_end = B.t_end[net_index];
   A.max_events = B.max_events;
   A.seed = B.seed;
@@ -66,10 +67,18 @@ __device__ __forceinline__ RunArgs item_args(const BatchArgs &B, int net_index, 
   A.sample_dt = 0.0;
   A.G = 0;
   memset(&A.out, 0, sizeof(A.out));
-  A.out.x_final_dev = B.x_final ? B.x_final + B.n_traj * bn.xoff : nullptr;
-  A.out.n_events_dev = B.n_events ? B.n_events + (int64_t)net_index * B.n_traj : nullptr;
-  A.out.status_dev = B.status ? B.status + (int64_t)net_index * B.n_traj : nullptr;
-  A.out.t_last_dev = B.t_last ? B.t_last + (int64_t)net_index * B.n_traj : nullptr;
+  const rt_batch_outputs &o = B.out;
+  const int64_t row = (int64_t)net_index * B.n_traj;  // first [net][traj] row of this network
+  A.out.x_final_dev = o.x_final_dev ? o.x_final_dev + B.n_traj * bn.xoff : nullptr;
+  A.out.n_events_dev = o.n_events_dev ? o.n_events_dev + row : nullptr;
+  A.out.status_dev = o.status_dev ? o.status_dev + row : nullptr;
+  A.out.t_last_dev = o.t_last_dev ? o.t_last_dev + row : nullptr;
+  A.out.loglik_dev = o.loglik_dev ? o.loglik_dev + row : nullptr;
+  A.out.counts_dev = o.counts_dev ? o.counts_dev + B.n_traj * bn.moff : nullptr;
+  A.out.t_internal_dev = o.t_internal_dev ? o.t_internal_dev + B.n_traj * bn.moff : nullptr;
+  A.out.trace_len = o.trace_len;
+  A.out.trace_mu_dev = o.trace_mu_dev ? o.trace_mu_dev + row * o.trace_len : nullptr;
+  A.out.trace_t_dev = o.trace_t_dev ? o.trace_t_dev + row * o.trace_len : nullptr;
   return A;
 }
 
@@ -78,6 +87,7 @@ __device__ __forceinline__ RunArgs item_args(const BatchArgs &B, int net_index, 
 // dependent loads, one thread's Exp(1) draw per event), and a second block on the SM
 // runs while the first waits -- measured 1.28x the single-block kernel on the 4096-network
 // batch.
+template <bool LL>
 __global__ void __launch_bounds__(512, 2) k_batch(const BatchArgs B) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long s_task;
@@ -99,10 +109,10 @@ __global__ void __launch_bounds__(512, 2) k_batch(const BatchArgs B) {
       const BlockNet net{bn.d.M, bn.d.N, bn.d.rdesc, bn.d.c, bn.d.vptr, bn.d.vlist, bn.d.sptr, bn.d.slist};
       const int tf = isfinite(A.t_end) ? 1 : 0;
       switch (bn.R) {
-        case 1: block_trajectory<1, false>(A, net, S, j, tf); break;
-        case 2: block_trajectory<2, false>(A, net, S, j, tf); break;
-        case 4: block_trajectory<4, false>(A, net, S, j, tf); break;
-        default: block_trajectory<8, false>(A, net, S, j, tf); break;
+        case 1: block_trajectory<1, LL>(A, net, S, j, tf); break;
+        case 2: block_trajectory<2, LL>(A, net, S, j, tf); break;
+        case 4: block_trajectory<4, LL>(A, net, S, j, tf); break;
+        default: block_trajectory<8, LL>(A, net, S, j, tf); break;
       }
       continue;
     }
@@ -119,10 +129,10 @@ __global__ void __launch_bounds__(512, 2) k_batch(const BatchArgs B) {
         int *X = (int *)smem + warp * B.maxN_warp;
         const int tf = isfinite(A.t_end) ? 1 : 0;
         switch (bn.R) {
-          case 1: warp_trajectory<1, false>(A, net, X, nullptr, j, tf); break;
-          case 2: warp_trajectory<2, false>(A, net, X, nullptr, j, tf); break;
-          case 4: warp_trajectory<4, false>(A, net, X, nullptr, j, tf); break;
-          default: warp_trajectory<8, false>(A, net, X, nullptr, j, tf); break;
+          case 1: warp_trajectory<1, LL>(A, net, X, nullptr, j, tf); break;
+          case 2: warp_trajectory<2, LL>(A, net, X, nullptr, j, tf); break;
+          case 4: warp_trajectory<4, LL>(A, net, X, nullptr, j, tf); break;
+          default: warp_trajectory<8, LL>(A, net, X, nullptr, j, tf); break;
         }
       }
       continue;
@@ -145,7 +155,7 @@ __global__ void __launch_bounds__(512, 2) k_batch(const BatchArgs B) {
         S.X = (int *)smem;
         S.mom = nullptr;
         S.mt = mom_table(nullptr, 0, 1);
-        simulate_one<8, false>(A, S, j, BT, isfinite(A.t_end) ? 1 : 0, 0);
+        simulate_one<8, LL>(A, S, j, BT, isfinite(A.t_end) ? 1 : 0, 0);
       }
     }
   }
@@ -172,8 +182,8 @@ struct rt_batch {
 
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-extern "C" int rt_batch_create(int32_t n_nets, const rt_network *const *nets, const rt_batch_policy *policy,
-                               rt_batch **out) {
+extern "C" int rt_batch_create(int32_t n_nets, const rt_network *const *nets, const uint32_t *stream_ids,
+                               const rt_batch_policy *policy, rt_batch **out) {
   clear_error();
   if (!out) return set_error(RT_ERR_INVALID_ARG, "rt_batch_create: out is NULL");
   *out = nullptr;
@@ -224,8 +234,11 @@ extern "C" int rt_batch_create(int32_t n_nets, const rt_network *const *nets, co
     if (cls == CLS_WARP) b->maxN_warp = std::max(b->maxN_warp, N);
     if (cls == CLS_THREAD) b->maxN_thread = std::max(b->maxN_thread, N);
     hn[i].xoff = b->total_species;
+    hn[i].moff = b->total_reactions;
     hn[i].cls = cls;
     hn[i].R = R;
+    hn[i].stream_id = stream_ids ? stream_ids[i] : (uint32_t)i;
+    hn[i].pad = 0;
     b->total_species += N;
     b->total_reactions += M;
     b->n_cls[cls]++;
@@ -292,10 +305,13 @@ extern "C" int rt_batch_create(int32_t n_nets, const rt_network *const *nets, co
     delete b;
     return set_error(RT_ERR_UNSUPPORTED, "batch networks need %zu bytes of shared memory", need);
   }
-  if (b->smem > 48 * 1024) cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
-  int per_sm = 0, sms = 0;
+  raise_smem_limit((const void *)k_batch<false>, b->smem);
+  raise_smem_limit((const void *)k_batch<true>, b->smem);
+  int per_sm = 0, per_sm_ll = 0, sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BT, b->smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<false>, BT, b->smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_ll, k_batch<true>, BT, b->smem);
+  per_sm = std::min(per_sm, per_sm_ll);
   if (per_sm < 1) per_sm = 1;
   if (pol.blocks_per_sm > 0) per_sm = std::min(per_sm, pol.blocks_per_sm);
   b->grid = per_sm * sms;
@@ -322,13 +338,13 @@ extern "C" int rt_batch_info(const rt_batch *b, int64_t *total_species, int64_t 
 }
 
 extern "C" int rt_batch_run(rt_batch *b, const int32_t *x0_dev, const double *t_end_dev, int64_t max_events,
-                            uint64_t seed, int64_t n_traj_per_net, int32_t *x_final_dev, int64_t *n_events_dev,
-                            int32_t *status_dev, double *t_last_dev, void *stream) {
+                            uint64_t seed, int64_t n_traj_per_net, const rt_batch_outputs *outputs, void *stream) {
   clear_error();
   if (!b) return set_error(RT_ERR_INVALID_ARG, "rt_batch_run: NULL batch");
   if (n_traj_per_net < 0) return set_error(RT_ERR_INVALID_ARG, "n_traj_per_net must be >= 0");
   if (max_events < 0 || max_events > INT32_MAX) return set_error(RT_ERR_INVALID_ARG, "max_events must be in [0, INT32_MAX]");
   if (!x0_dev || !t_end_dev) return set_error(RT_ERR_INVALID_ARG, "x0 and t_end are required");
+  if (outputs && outputs->trace_len < 0) return set_error(RT_ERR_INVALID_ARG, "trace_len must be >= 0");
   int dev = -1;
   cudaGetDevice(&dev);
   if (dev != b->device) return set_error(RT_ERR_INVALID_ARG, "batch lives on device %d, device %d is current", b->device, dev);
@@ -350,10 +366,8 @@ extern "C" int rt_batch_run(rt_batch *b, const int32_t *x0_dev, const double *t_
   A.t_end = t_end_dev;
   A.max_events = (int32_t)max_events;
   A.seed = seed;
-  A.x_final = x_final_dev;
-  A.n_events = n_events_dev;
-  A.status = status_dev;
-  A.t_last = t_last_dev;
+  memset(&A.out, 0, sizeof(A.out));
+  if (outputs) A.out = *outputs;
   A.maxN_thread = b->maxN_thread;
   A.maxN_warp = b->maxN_warp;
   A.maxM_block = b->maxM_block;
@@ -362,7 +376,8 @@ extern "C" int rt_batch_run(rt_batch *b, const int32_t *x0_dev, const double *t_
   cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return set_error(RT_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
   const int grid = (int)std::min<int64_t>(b->grid, std::max<int64_t>(1, A.n_tasks));
-  k_batch<<<grid, BT, b->smem, s>>>(A);
+  if (A.out.loglik_dev) k_batch<true><<<grid, BT, b->smem, s>>>(A);
+  else k_batch<false><<<grid, BT, b->smem, s>>>(A);
   e = cudaGetLastError();
   return e == cudaSuccess ? RT_OK : set_error(RT_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
 }

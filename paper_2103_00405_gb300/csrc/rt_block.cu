@@ -27,7 +27,7 @@ template <int R>
 static cudaError_t launch_r(const RunArgs &a, int B, cudaStream_t s, int tf) {
   const size_t smem = block_scratch_bytes(a.net.M, a.net.N, B);
   auto kern = a.out.loglik_dev ? k_ens_block<R, true> : k_ens_block<R, false>;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit((const void *)kern, smem);
   int per_sm = 0, dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -25,7 +25,6 @@
 #include <climits>
 #include <cmath>
 #include <cstdlib>
-#include <mutex>
 
 #include "rt_filter.cuh"
 #include "rt_sim.cuh"
@@ -451,6 +450,7 @@ __global__ void __launch_bounds__(kBundleThreads) k_bundle(const BundleArgs B) {
         }
       }
       t = tn;
+      if (c == 0 && tid == 0) trace_event(r.out, j, ev, mu, tn);
       if (LL && c == 0 && tid == 0) ll = __dadd_rn(ll, rt_ln(dec.a_mu));
       __syncthreads();  // everyone has read Xs for this event
       if (tid == 0)
@@ -493,6 +493,7 @@ __global__ void __launch_bounds__(kBundleThreads) k_bundle(const BundleArgs B) {
   }
   if (c == 0) {
     __syncthreads();
+    trace_tail(r.out, j, ev, tid, blockDim.x);
     if (r.out.x_final_dev)
       for (int s = tid; s < N; s += blockDim.x) r.out.x_final_dev[j * N + s] = Xs[s];
     if (tid == 0) {
@@ -559,7 +560,7 @@ static int bundle_capacity(size_t smem, bool ll) {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (smem > (size_t)optin - 1024) return 0;  // static shared memory (barriers) included
   auto kern = ll ? k_bundle<true> : k_bundle<false>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+  if (raise_smem_limit((const void *)kern, smem) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBundleThreads, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -618,15 +619,17 @@ int launch_bundle_mapping(const RunArgs &a, int ctas_per_traj, void *ws, size_t 
   if (const char *env = getenv("RT_DEBUG_SPIN_LIMIT")) spin = atoll(env);
   B.spin_limit = spin;
   B.traj0 = 0;
+  // every check comes before the first enqueued operation: a refused launch leaves
+  // the stream, the workspace and the outputs untouched
+  auto kern = ll ? k_bundle<true> : k_bundle<false>;
+  const int64_t cap = bundle_capacity(p.smem, ll);
+  if (cap < C) return set_error(RT_ERR_UNSUPPORTED, "bundle of %d blocks cannot be co-resident (capacity %lld)", C, (long long)cap);
+  const int64_t per_wave = cap / C;
   cudaError_t e = cudaMemsetAsync(B.bar, 0, sizeof(unsigned long long) * a.n_traj, s);
   if (e != cudaSuccess) return set_error(RT_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
   k_bundle_init<<<152 * 8, 256, 0, s>>>(B);
   if ((e = cudaGetLastError()) != cudaSuccess) return set_error(RT_ERR_CUDA, "init launch: %s", cudaGetErrorString(e));
 
-  auto kern = ll ? k_bundle<true> : k_bundle<false>;
-  const int64_t cap = bundle_capacity(p.smem, ll);
-  if (cap < C) return set_error(RT_ERR_UNSUPPORTED, "bundle of %d blocks cannot be co-resident (capacity %lld)", C, (long long)cap);
-  const int64_t per_wave = cap / C;
   for (int64_t t0 = 0; t0 < a.n_traj; t0 += per_wave) {
     B.traj0 = t0;
     const int64_t nw = std::min<int64_t>(per_wave, a.n_traj - t0);
@@ -656,35 +659,27 @@ int launch_bundle_mapping(const RunArgs &a, int ctas_per_traj, void *ws, size_t 
 // The array is a file-scope __device__ variable: every GPU that loads this library
 // holds kNoAllocScratchBytes of it until the process exits.  In host code the
 // array's name is only a host-side stand-in, so its device address is obtained with
-// cudaGetSymbolAddress, once per device, by the first call on that device (with the
-// device current); that first call should come before any stream capture.  Every
-// call on a device uses the same array and leaves its contents behind; the launch
-// zeroes what must start at zero (the barrier counters) and initialises the rest.
-// Calls whose work overlaps on the GPU (different streams, or threads without
-// ordering) race on the array: order them on one stream or synchronise between them.
+// cudaGetSymbolAddress, by every call (with the calling device current; the lookup
+// allocates nothing and is cheap, and it stays right if the device's context is
+// torn down and re-created between calls, where the module and its array may be
+// loaded at a new address).  The first call on a device loads the library's module
+// there, so it should come before any stream capture.  Every call on a device uses
+// the same array and leaves its contents behind; the launch zeroes what must start
+// at zero (the barrier counters) and initialises the rest.  Calls whose work
+// overlaps on the GPU (different streams, or threads without ordering) race on the
+// array: order them on one stream or synchronise between them.
 // ----------------------------------------------------------------------------------
 
 constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-static std::mutex g_noalloc_mutex;
-static void *g_noalloc_ptr[64] = {nullptr};
-
-// Device address of the scratch array on the current device (set up once per device).
+// Device address of the scratch array on the current device.
 static int noalloc_scratch(void **out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return set_error(RT_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-  if (dev < 0 || dev >= 64) return set_error(RT_ERR_UNSUPPORTED, "device %d: at most 64 devices are supported", dev);
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return set_error(RT_ERR_CUDA, "cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return set_error(RT_ERR_CUDA, "cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
+  *out = p;
   return RT_OK;
 }
 

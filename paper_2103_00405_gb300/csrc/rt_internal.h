@@ -61,6 +61,13 @@ namespace rt {
 int set_error(int code, const char *fmt, ...);
 void clear_error();
 
+// Raise a kernel's dynamic shared-memory limit on the current device to at least
+// `bytes` (never lowers it).  The limit is a property of the kernel, shared by
+// every caller and thread of the process, so lowering it for one launch could
+// break another that is already configured (or captured in a graph); a
+// process-wide running maximum per (kernel, device) is kept under a mutex.
+cudaError_t raise_smem_limit(const void *kernel, size_t bytes);
+
 // Arguments of a simulation launch (plain data, passed by value to kernels).
 struct RunArgs {
   DevNet net;

@@ -112,7 +112,7 @@ inline int moment_cluster(const RunArgs &a) {
 template <typename... Params, typename... Args>
 cudaError_t launch_clustered(void (*kern)(Params...), unsigned grid, int block, size_t smem, cudaStream_t s, int cl,
                              Args... args) {
-  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit((const void *)kern, smem);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);

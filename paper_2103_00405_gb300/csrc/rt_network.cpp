@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include "rt_internal.h"
@@ -38,6 +39,21 @@ int set_error(int code, const char *fmt, ...) {
 void clear_error() { g_err.clear(); }
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+cudaError_t raise_smem_limit(const void *kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, size_t> current;
+  if (bytes <= 48 * 1024) return cudaSuccess;  // the default limit
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t &cur = current[{kernel, dev}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 
 }  // namespace rt
 

@@ -106,6 +106,24 @@ __device__ __forceinline__ float wait_estimate(double P, double T, double a) {
   return rem > 0.0f ? __fdividef(rem, f32_lower(a) + 1e-37f) : 0.0f;
 }
 
+// Per-event trace: event ev of trajectory j fired channel mu at time t (recorded for
+// the first trace_len events).
+__device__ __forceinline__ void trace_event(const rt_outputs &o, int64_t j, int32_t ev, int mu, double t) {
+  if (ev < o.trace_len) {
+    if (o.trace_mu_dev) o.trace_mu_dev[j * o.trace_len + ev] = mu;
+    if (o.trace_t_dev) o.trace_t_dev[j * o.trace_len + ev] = t;
+  }
+}
+
+// The unused rest of trajectory j's trace, entries [ev, trace_len): -1 and 0, written
+// by nthr cooperating threads (this one is number tid).
+__device__ __forceinline__ void trace_tail(const rt_outputs &o, int64_t j, int32_t ev, int tid, int nthr) {
+  for (int64_t e = (int64_t)ev + tid; e < o.trace_len; e += nthr) {
+    if (o.trace_mu_dev) o.trace_mu_dev[j * o.trace_len + e] = -1;
+    if (o.trace_t_dev) o.trace_t_dev[j * o.trace_len + e] = 0.0;
+  }
+}
+
 // Register-array element r (runtime) by predicated selects, so arrays indexed with
 // compile-time indices stay in registers.
 template <int R, typename T>

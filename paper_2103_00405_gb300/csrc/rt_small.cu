@@ -155,6 +155,7 @@ __device__ __forceinline__ void simulate_small(const RunArgs &A, const SmallNet 
         next_g = __dmul_rn(__ll2double_rn(gi), A.sample_dt);
       }
       t = tn;
+      trace_event(A.out, j, ev, mu, tn);
       // every internal time advances by a_k dt (Eq. 17)
       double a_mu = 0.0;
 #pragma unroll
@@ -218,6 +219,7 @@ __device__ __forceinline__ void simulate_small(const RunArgs &A, const SmallNet 
 #pragma unroll
     for (int s = 0; s < NMAX; ++s)
       if (s < N) A.out.x_final_dev[j * N + s] = X[s];
+  trace_tail(A.out, j, ev, 0, 1);
   if (A.out.n_events_dev) A.out.n_events_dev[j] = ev;
   if (A.out.status_dev) A.out.status_dev[j] = status;
   if (A.out.t_last_dev) A.out.t_last_dev[j] = t;

@@ -301,6 +301,7 @@ __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNe
         break;
       }
       t = tn;
+      if (tid == 0) trace_event(A.out, j, ev, bk, tn);
       ++ev;
       dmin = dnext;
       mu = bk;
@@ -338,6 +339,7 @@ __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNe
     for (int k = tid; k < M; k += B) A.out.counts_dev[j * M + k] = S.NK[k];
   if (A.out.x_final_dev)
     for (int s = tid; s < N; s += B) A.out.x_final_dev[j * N + s] = X[s];
+  trace_tail(A.out, j, ev, tid, B);
   if (tid == 0) {
     if (A.out.n_events_dev) A.out.n_events_dev[j] = ev;
     if (A.out.status_dev) A.out.status_dev[j] = status;

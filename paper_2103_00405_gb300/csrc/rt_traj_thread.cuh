@@ -178,6 +178,7 @@ __device__ __forceinline__ void simulate_one(const RunArgs &A, const ThreadNet &
         next_g = __dmul_rn(__ll2double_rn(gi), A.sample_dt);
       }
       t = tn;
+      trace_event(A.out, j, ev, mu, tn);
       // every internal time advances by a_k dt (Eq. 17)
       double a_mu = 0.0;
 #pragma unroll
@@ -245,6 +246,7 @@ __device__ __forceinline__ void simulate_one(const RunArgs &A, const ThreadNet &
       if (k < M) A.out.counts_dev[j * M + k] = n[k];
   if (A.out.x_final_dev)
     for (int s = 0; s < N; ++s) A.out.x_final_dev[j * N + s] = X[s * B];
+  trace_tail(A.out, j, ev, 0, 1);
   if (A.out.n_events_dev) A.out.n_events_dev[j] = ev;
   if (A.out.status_dev) A.out.status_dev[j] = status;
   if (A.out.t_last_dev) A.out.t_last_dev[j] = t;

@@ -184,6 +184,7 @@ __device__ __forceinline__ void warp_trajectory(const RunArgs &A, const WarpNet 
         next_g = __dmul_rn(__ll2double_rn(gi), A.sample_dt);
       }
       t = tn;
+      if (lane == 0) trace_event(A.out, j, ev, mu, tn);
       // The fired channel's new Exp(1) increment (Eq. 27) is -ln u and, with the
       // likelihood, ln a_mu is needed too: the owner lane and its neighbour prepare
       // their arguments, then run one fixed-point logarithm side by side.
@@ -260,6 +261,7 @@ __device__ __forceinline__ void warp_trajectory(const RunArgs &A, const WarpNet 
       if (lane + 32 * r < M) A.out.counts_dev[j * M + lane + 32 * r] = n[r];
   if (A.out.x_final_dev)
     for (int s = lane; s < N; s += 32) A.out.x_final_dev[j * N + s] = X[s];
+  trace_tail(A.out, j, ev, lane, 32);
   if (lane == 0) {
     if (A.out.n_events_dev) A.out.n_events_dev[j] = ev;
     if (A.out.status_dev) A.out.status_dev[j] = status;

@@ -71,7 +71,7 @@ static cudaError_t launch_r(const RunArgs &a, cudaStream_t s, int tend_finite) {
   const size_t smem = warp_net_bytes(a.net) + mom + (size_t)a.net.N * 4 * wpb;
   const unsigned grid = (unsigned)((a.n_traj + wpb - 1) / wpb);
   auto kern = a.out.loglik_dev ? k_ens_warp<R, true> : k_ens_warp<R, false>;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit((const void *)kern, smem);
   kern<<<grid, kWarpBlock, smem, s>>>(a, tend_finite, mom ? 1 : 0);
   return cudaGetLastError();
 }
