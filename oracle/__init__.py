@@ -11,7 +11,8 @@ Functions (all follow Liu & Wang, arXiv:2103.00405):
   rt_log         -- fixed-point natural log rounded once to binary64
   exp1 / uniform -- the Exp(1) internal-time increment of Eq. 24 and its uniform
   grid_len       -- number of sampling points on [0, t_end]
-  run            -- the NRRTA loop of Table 2 (Eq. 24-27) for many trajectories
+  run            -- the NRRTA loop of Table 2 (Eq. 24-27) for many trajectories, in the
+                    internal-time form or the absolute-time (dependency graph) form
   loglik_backward-- d(sum_j w_j l_j)/dc from saved counts and internal times
 """
 from __future__ import annotations
@@ -56,7 +57,7 @@ def _declare(lib):
     lib.oracle_uniform.restype = dbl
     lib.oracle_grid_len.argtypes = [dbl, dbl]
     lib.oracle_grid_len.restype = i64
-    lib.oracle_run.argtypes = [i32, i32, i64, vp, vp, vp, i64, vp, vp, vp, vp, vp, i32,
+    lib.oracle_run.argtypes = [i32, i32, i32, i64, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, i32,
                                dbl, i64, u64, u32, i64, i64, dbl,
                                vp, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, i32]
     lib.oracle_run.restype = ctypes.c_int
@@ -106,11 +107,17 @@ def grid_len(t_end: float, sample_dt: float, lib=None) -> int:
     return int((lib or load()).oracle_grid_len(float(t_end), float(sample_dt)))
 
 
+MODE_EAGER, MODE_LAZY = 0, 1
+
+
 def run(net, x0, t_end, n_traj, seed=1, stream_id=0, traj_offset=0, max_events=(1 << 31) - 1,
-        sample_dt=0.0, want_grid=False, want_grad=False, trace_len=0, n_threads=1, lib=None):
+        sample_dt=0.0, want_grid=False, want_grad=False, trace_len=0, n_threads=1, lib=None,
+        mode=MODE_EAGER, enabled=None):
     """Run the oracle; returns a dict of numpy arrays.
 
-    x0 is [N] (shared) or [n_traj, N] (per trajectory).
+    x0 is [N] (shared) or [n_traj, N] (per trajectory).  mode: MODE_EAGER (Table 2 in
+    internal-time form) or MODE_LAZY (absolute-time form with the dependency graph).
+    enabled: optional [M] flags; channels with 0 never fire (frozen internal time).
     """
     lib = lib or load()
     N, M = int(net.n_species), int(net.n_reactions)
@@ -133,9 +140,12 @@ def run(net, x0, t_end, n_traj, seed=1, stream_id=0, traj_offset=0, max_events=(
     if trace_len:
         out["trace_mu"] = np.zeros((n_traj, trace_len), np.int32)
         out["trace_t"] = np.zeros((n_traj, trace_len), np.float64)
-    rc = lib.oracle_run(N, M, len(net.reac_rxn), _p(net.reac_rxn), _p(net.reac_sp), _p(net.reac_coef),
+    en = None if enabled is None else np.ascontiguousarray(enabled, dtype=np.uint8)
+    if en is not None and en.shape != (M,):
+        raise ValueError("enabled must have one entry per reaction")
+    rc = lib.oracle_run(int(mode), N, M, len(net.reac_rxn), _p(net.reac_rxn), _p(net.reac_sp), _p(net.reac_coef),
                         len(net.stoi_rxn), _p(net.stoi_rxn), _p(net.stoi_sp), _p(net.stoi_delta),
-                        _p(net.c), _p(x0), per, float(t_end), int(max_events), int(seed), int(stream_id),
+                        _p(net.c), _p(en), _p(x0), per, float(t_end), int(max_events), int(seed), int(stream_id),
                         n_traj, int(traj_offset), float(sample_dt),
                         _p(out["x_final"]), _p(out.get("grid")), _p(out["n_events"]), _p(out["status"]),
                         _p(out["t_last"]), _p(out.get("loglik")), _p(out.get("counts")),

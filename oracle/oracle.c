@@ -34,6 +34,22 @@
  * [sqrt(1/2), sqrt(2)), and ln(m) = 2 atanh(s), s = (m - 1)/(m + 1), with the
  * atanh power series 2 s (1 + s^2/3 + s^4/5 + ...).
  *
+ * Modes (oracle_run's `mode`):
+ *   0  Table 2 in the internal-time form above: every internal time advances at
+ *      every event, T_k += a_k dt, and the waiting times (P_k - T_k) / a_k are
+ *      recomputed for all channels.
+ *   1  the same method in absolute-time ("lazy") form, the Gibson-Bruck next
+ *      reaction method with the dependency graph the paper describes (Sec. 5):
+ *      each channel keeps the real time s_k of its last update and its absolute
+ *      firing time tau_k = s_k + (P_k - T_k) / a_k; an event at tau_mu touches
+ *      only mu and the channels that read a species the event changed (their
+ *      internal time is first brought up to the event, T_k += a_k (t - s_k), then
+ *      a_k and tau_k are recomputed); every other tau_k stays as it is.  In exact
+ *      arithmetic both modes give the same path; their roundings differ.
+ * enabled (NULL = all): a channel with enabled[k] == 0 is forbidden to fire; its
+ * propensity is taken as 0, so its internal time is frozen (Table 2's note on
+ * boundary conditions).
+ *
  * ORACLE_MUTANT (0 by default) plants one deliberate mistake per value, used only
  * by the mutation test to show that the pins catch such mistakes.
  */
@@ -223,6 +239,7 @@ typedef struct {
   int64_t *vptr; /* net change of reaction k: vsp/vdel[vptr[k] .. vptr[k+1]) */
   int32_t *vsp, *vdel;
   const double *c;
+  const uint8_t *enabled; /* NULL: every channel may fire */
 } onet;
 
 /* Group COO entries by reaction; entries for the same (reaction, species) are summed
@@ -281,6 +298,7 @@ static int64_t binom(int64_t x, int32_t s) {
 
 /* a_k = c_k * h_k(X), h_k = prod_j binom(X_j, sigma_jk) (Eq. 1-2) */
 static double propensity(const onet *g, int32_t k, const int32_t *X) {
+  if (g->enabled && !g->enabled[k]) return 0.0; /* forbidden channel: frozen internal time */
   int64_t h = 1;
   for (int64_t i = g->rptr[k]; i < g->rptr[k + 1]; i++)
     h *= binom(X[g->rsp[ORACLE_MUTANT == 2 ? g->rptr[k] : i]], g->rcoef[i]);
@@ -300,6 +318,7 @@ int64_t oracle_grid_len(double t_end, double sample_dt) {
 
 typedef struct {
   const onet *g;
+  int32_t mode;
   const int32_t *x0; int per_traj_x0;
   double t_end; int64_t max_events;
   uint64_t seed; uint32_t stream; int64_t traj_offset;
@@ -430,43 +449,176 @@ static void run_traj(const job_t *J, int64_t j, double *P, double *T, double *a,
   if (J->t_last) J->t_last[j] = t;
 }
 
+/* Absolute firing time of a channel updated at real time su: su + (P - T) / a
+ * (0 remaining internal time gives su), +inf for a = 0 (mode 1). */
+static double lazy_tau(double P, double T, double a, double su) {
+  if (a == 0.0) return INFINITY;
+  double rem = P - T;
+  double w = rem > 0.0 ? rem / a : 0.0;
+  return ORACLE_MUTANT == 17 ? w : su + w;
+}
+
+/* Mode 1: the absolute-time form (see the header).  s[k] is the real time up to
+ * which T[k] is accounted, tau[k] the absolute firing time; upd[k] flags the
+ * channels an event touches and chg[i] the species it changed. */
+static void run_traj_lazy(const job_t *J, int64_t j, double *P, double *T, double *a, int32_t *n, int32_t *X,
+                          double *s, double *tau, uint8_t *upd, uint8_t *chg) {
+  const onet *g = J->g;
+  const int32_t N = g->N, M = g->M;
+  const uint64_t gid = (uint64_t)(J->traj_offset + j);
+  const int32_t *x0 = J->x0 + (J->per_traj_x0 ? j * (int64_t)N : 0);
+  int32_t *grid = J->grid ? J->grid + j * J->G * N : NULL;
+  int32_t *trace_mu = J->trace_mu ? J->trace_mu + j * J->trace_len : NULL;
+  double *trace_t = J->trace_t ? J->trace_t + j * J->trace_len : NULL;
+  for (int64_t i = 0; i < J->trace_len; i++) {
+    if (trace_mu) trace_mu[i] = -1;
+    if (trace_t) trace_t[i] = 0.0;
+  }
+
+  int32_t status = ST_TEND;
+  int bad = 0;
+  for (int32_t i = 0; i < N; i++) {
+    X[i] = x0[i];
+    chg[i] = 0;
+    if (x0[i] < 0) bad = 1;
+  }
+  double t = 0.0, ll = 0.0;
+  int64_t ev = 0, gi = 0;
+  for (int32_t k = 0; k < M; k++) { n[k] = 0; T[k] = 0.0; s[k] = 0.0; a[k] = 0.0; }
+
+  if (bad) {
+    status = ST_BAD_X0;
+  } else {
+    for (int32_t k = 0; k < M; k++) {
+      P[k] = oracle_exp1(J->seed, gid, (uint32_t)k, 0, J->stream);
+      a[k] = propensity(g, k, X);
+      tau[k] = lazy_tau(P[k], T[k], a[k], 0.0);
+    }
+    for (;;) {
+      /* the earliest absolute firing time; ties go to the smallest index */
+      double tmin = INFINITY;
+      int32_t mu = -1;
+      for (int32_t k = 0; k < M; k++)
+        if (tau[k] < tmin) { tmin = tau[k]; mu = k; }
+      if (mu < 0) { status = ST_ABSORBED; break; }
+      double tn = tmin;
+      if (tn > J->t_end) { status = ST_TEND; break; }
+      if (ev == J->max_events) { status = ST_MAX_EVENTS; break; }
+      int over = 0;
+      for (int64_t i = g->vptr[mu]; i < g->vptr[mu + 1]; i++) {
+        int64_t nx = (int64_t)X[g->vsp[i]] + g->vdel[i];
+        if (nx > INT32_MAX || nx < 0) over = 1;
+      }
+      if (over) { status = ST_OVERFLOW; break; }
+      if (grid)
+        while (gi < J->G && (double)gi * J->sample_dt < tn) {
+          memcpy(grid + gi * N, X, sizeof(int32_t) * (size_t)N);
+          gi++;
+        }
+      else
+        while (gi < J->G && (double)gi * J->sample_dt < tn) gi++;
+      t = tn;
+      if (J->loglik) ll = ll + oracle_rt_log(a[mu]);
+      /* fire: X += v_mu (Eq. 5); the species it changed */
+      for (int64_t i = g->vptr[mu]; i < g->vptr[mu + 1]; i++) {
+        X[g->vsp[i]] += g->vdel[i];
+        chg[g->vsp[i]] = 1;
+      }
+      if (trace_mu && ev < J->trace_len) { trace_mu[ev] = mu; trace_t[ev] = t; }
+      n[mu] += 1;
+      ev += 1;
+      /* the channels the event touches: mu, and every channel with a reactant species
+       * among the changed ones (the dependency graph, Sec. 5) */
+      for (int32_t k = 0; k < M; k++) {
+        upd[k] = k == mu;
+        for (int64_t i = g->rptr[k]; i < g->rptr[k + 1]; i++)
+          if (chg[g->rsp[i]] && !(ORACLE_MUTANT == 16 && i > g->rptr[k])) upd[k] = 1;
+      }
+      /* their internal times are brought up to the event with the old propensities (Eq. 17) */
+      for (int32_t k = 0; k < M; k++)
+        if (upd[k]) {
+          if (!(ORACLE_MUTANT == 15 && k != mu)) T[k] = T[k] + a[k] * (t - s[k]);
+          s[k] = t;
+        }
+      /* only the fired channel draws a new increment (Eq. 27) */
+      P[mu] = P[mu] + oracle_exp1(J->seed, gid, (uint32_t)mu, (uint64_t)n[mu], J->stream);
+      /* new propensities (Eq. 1-2) and absolute firing times of the touched channels */
+      for (int32_t k = 0; k < M; k++)
+        if (upd[k]) {
+          a[k] = propensity(g, k, X);
+          tau[k] = lazy_tau(P[k], T[k], a[k], t);
+        }
+      for (int64_t i = g->vptr[mu]; i < g->vptr[mu + 1]; i++) chg[g->vsp[i]] = 0;
+    }
+  }
+
+  if (grid)
+    for (; gi < J->G; gi++)
+      for (int32_t i = 0; i < N; i++)
+        grid[gi * N + i] = (status == ST_TEND || status == ST_ABSORBED) ? X[i] : -1;
+
+  if (status != ST_BAD_X0 && ORACLE_MUTANT != 18) {
+    /* every channel's internal time up to the end of the run: t_end if the path
+     * reached it (or was absorbed before a finite t_end), else the last event */
+    double tf = ((status == ST_TEND || status == ST_ABSORBED) && isfinite(J->t_end)) ? J->t_end : t;
+    for (int32_t k = 0; k < M; k++) T[k] = T[k] + a[k] * (tf - s[k]);
+  }
+  if (J->loglik) {
+    double sT = 0.0;
+    for (int32_t k = 0; k < M; k++) sT = sT + T[k];
+    J->loglik[j] = status == ST_BAD_X0 ? NAN : ll - sT;
+  }
+  if (J->counts) memcpy(J->counts + j * (int64_t)M, n, sizeof(int32_t) * (size_t)M);
+  if (J->t_internal) memcpy(J->t_internal + j * (int64_t)M, T, sizeof(double) * (size_t)M);
+  if (J->x_final) memcpy(J->x_final + j * (int64_t)N, X, sizeof(int32_t) * (size_t)N);
+  if (J->n_events) J->n_events[j] = ev;
+  if (J->status) J->status[j] = status;
+  if (J->t_last) J->t_last[j] = t;
+}
+
 static void *worker(void *arg) {
   job_t *J = (job_t *)arg;
   int32_t M = J->g->M, N = J->g->N;
   double *P = malloc(sizeof(double) * (size_t)M), *T = malloc(sizeof(double) * (size_t)M);
   double *a = malloc(sizeof(double) * (size_t)M);
   int32_t *n = malloc(sizeof(int32_t) * (size_t)M), *X = malloc(sizeof(int32_t) * (size_t)N);
-  if (!P || !T || !a || !n || !X) {
+  double *s = malloc(sizeof(double) * (size_t)M), *tau = malloc(sizeof(double) * (size_t)M);
+  uint8_t *upd = malloc((size_t)M), *chg = malloc((size_t)N);
+  if (!P || !T || !a || !n || !X || !s || !tau || !upd || !chg) {
     J->err = -4;
   } else {
-    for (int64_t j = J->j0; j < J->j1; j++) run_traj(J, j, P, T, a, n, X);
+    for (int64_t j = J->j0; j < J->j1; j++) {
+      if (J->mode == 1) run_traj_lazy(J, j, P, T, a, n, X, s, tau, upd, chg);
+      else run_traj(J, j, P, T, a, n, X);
+    }
   }
-  free(P); free(T); free(a); free(n); free(X);
+  free(P); free(T); free(a); free(n); free(X); free(s); free(tau); free(upd); free(chg);
   return NULL;
 }
 
 /*
- * Run n_traj trajectories (global ids traj_offset + j) of one network.
+ * Run n_traj trajectories (global ids traj_offset + j) of one network in the given
+ * mode (0: Table 2 internal-time form, 1: absolute-time form; see the header).
  * Output arrays may be NULL.  Returns 0, -1 for invalid arguments, -4 for
  * allocation failure.
  */
-int oracle_run(int32_t N, int32_t M,
+int oracle_run(int32_t mode, int32_t N, int32_t M,
                int64_t n_reac_nz, const int32_t *reac_rxn, const int32_t *reac_sp, const int32_t *reac_coef,
                int64_t n_stoi_nz, const int32_t *stoi_rxn, const int32_t *stoi_sp, const int32_t *stoi_delta,
-               const double *c, const int32_t *x0, int32_t per_traj_x0,
+               const double *c, const uint8_t *enabled, const int32_t *x0, int32_t per_traj_x0,
                double t_end, int64_t max_events, uint64_t seed, uint32_t stream,
                int64_t n_traj, int64_t traj_offset, double sample_dt,
                int32_t *x_final, int32_t *grid, int64_t *n_events, int32_t *status, double *t_last,
                double *loglik, int32_t *counts, double *t_internal,
                int64_t trace_len, int32_t *trace_mu, double *trace_t, int32_t n_threads) {
-  if (N < 1 || M < 1 || n_traj < 0 || max_events < 0 || t_end != t_end) return -1;
+  if (mode < 0 || mode > 1 || N < 1 || M < 1 || n_traj < 0 || max_events < 0 || t_end != t_end) return -1;
   for (int64_t i = 0; i < n_reac_nz; i++)
     if (reac_rxn[i] < 0 || reac_rxn[i] >= M || reac_sp[i] < 0 || reac_sp[i] >= N || reac_coef[i] <= 0)
       return -1;
   for (int64_t i = 0; i < n_stoi_nz; i++)
     if (stoi_rxn[i] < 0 || stoi_rxn[i] >= M || stoi_sp[i] < 0 || stoi_sp[i] >= N) return -1;
   onet g;
-  g.N = N; g.M = M; g.c = c;
+  g.N = N; g.M = M; g.c = c; g.enabled = enabled;
   if (group_coo(M, n_reac_nz, reac_rxn, reac_sp, reac_coef, &g.rptr, &g.rsp, &g.rcoef)) return -4;
   if (group_coo(M, n_stoi_nz, stoi_rxn, stoi_sp, stoi_delta, &g.vptr, &g.vsp, &g.vdel)) return -4;
 
@@ -478,7 +630,7 @@ int oracle_run(int32_t N, int32_t M,
   int rc = 0;
   for (int32_t w = 0; w < n_threads; w++) {
     job_t *J = &jobs[w];
-    J->g = &g; J->x0 = x0; J->per_traj_x0 = per_traj_x0;
+    J->g = &g; J->mode = mode; J->x0 = x0; J->per_traj_x0 = per_traj_x0;
     J->t_end = t_end; J->max_events = max_events; J->seed = seed; J->stream = stream;
     J->traj_offset = traj_offset; J->sample_dt = sample_dt; J->G = G;
     J->x_final = x_final; J->grid = grid; J->n_events = n_events; J->status = status; J->t_last = t_last;

@@ -8,6 +8,11 @@ Each mutant build of oracle.c plants one plausible mistake (ORACLE_MUTANT = n):
   9 refresh reuses the first draw of a channel 10 grid sampled after instead of before events
  11 likelihood with the integral's sign flipped 12 logarithm series truncated after two terms
  13 uniform mapping that can produce u = 0      14 Philox round mixing the wrong word
+In the absolute-time form (mode 1):
+ 15 touched channels' internal times not brought up to the event (other than the fired one)
+ 16 dependency test reads only a reaction's first reactant species
+ 17 absolute firing time computed without the update time (a relative waiting time)
+ 18 internal times not brought up to the end of the run
 The pin suite (tests/test_oracle_pins.py) must fail on every one of them.
 """
 import concurrent.futures
@@ -20,7 +25,7 @@ import pytest
 import oracle
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-MUTANTS = list(range(1, 15))
+MUTANTS = list(range(1, 19))
 
 
 def _run_pins(n, tmpdir):

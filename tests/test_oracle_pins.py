@@ -7,6 +7,12 @@ brute-force chemical master equation solutions (dimerisation, small
 Lotka-Volterra), the single-step law of the Markov jump process (Eq. 3, 19-23),
 exact invariants (Eq. 5), the random-time-change martingale (Eq. 16-18) and the
 exact likelihood of a pure-birth path.  All inputs are seeded.
+
+The simulation pins run in both of the oracle's modes: the internal-time form of
+Table 2 (every internal time advanced at every event) and the absolute-time form
+with the dependency graph (Sec. 5; only the fired channel and the channels reading
+a changed species are touched).  Further pins tie the two modes to each other (the
+same path up to rounding) and fix the frozen-channel rule of Table 2's note.
 """
 import math
 
@@ -19,6 +25,12 @@ import scipy.stats
 
 import oracle
 from paper_2103_00405_gb300 import workloads as W
+
+MODES = [oracle.MODE_EAGER, oracle.MODE_LAZY]
+
+
+def _run(mode, *args, **kw):
+    return oracle.run(*args, mode=mode, **kw)
 
 # ----------------------------------------------------------------------------------
 # Random numbers and logarithm
@@ -118,11 +130,12 @@ def _chi2_pvalue(counts, probs, min_expected=5.0):
     return scipy.stats.chi2.sf(stat, len(cb) - 1)
 
 
-def test_birth_death_transient_is_poisson(nthreads):
+@pytest.mark.parametrize("mode", MODES)
+def test_birth_death_transient_is_poisson(nthreads, mode):
     """0 -> A (k), A -> 0 (gamma A), A(0) = 0: A(t) ~ Poisson(k/gamma (1 - e^{-gamma t}))."""
     net = W.birth_death(100.0, 1.0)
     n_traj = 4000
-    o = oracle.run(net, [0], 10.0, n_traj, seed=11, sample_dt=0.25, want_grid=True, n_threads=nthreads)
+    o = _run(mode, net, [0], 10.0, n_traj, seed=11, sample_dt=0.25, want_grid=True, n_threads=nthreads)
     assert (o["status"] == oracle.ST_TEND).all()
     for t in (0.25, 1.0, 2.5, 10.0):
         gi = int(round(t / 0.25))
@@ -133,12 +146,13 @@ def test_birth_death_transient_is_poisson(nthreads):
         assert _chi2_pvalue(hist, scipy.stats.poisson.pmf(np.arange(400), lam)) > 1e-4
 
 
-def test_isomerisation_is_binomial(nthreads):
+@pytest.mark.parametrize("mode", MODES)
+def test_isomerisation_is_binomial(nthreads, mode):
     """A -> B (k1), B -> A (k2), A(0) = n: A(t) ~ Binomial(n, k2/(k1+k2) + k1/(k1+k2) e^{-(k1+k2) t})."""
     k1, k2, n0 = 1.0, 0.5, 50
     net = W.isomerisation(k1, k2)
     n_traj = 20000
-    o = oracle.run(net, [n0, 0], 3.0, n_traj, seed=5, sample_dt=0.1, want_grid=True, n_threads=nthreads)
+    o = _run(mode, net, [n0, 0], 3.0, n_traj, seed=5, sample_dt=0.1, want_grid=True, n_threads=nthreads)
     for t in (0.3, 1.0, 3.0):
         gi = int(round(t / 0.1))
         p = k2 / (k1 + k2) + k1 / (k1 + k2) * math.exp(-(k1 + k2) * t)
@@ -170,12 +184,13 @@ def _cme_transient(states, rates_fn, p0, times):
     return res
 
 
-def test_dimerisation_matches_master_equation(nthreads):
+@pytest.mark.parametrize("mode", MODES)
+def test_dimerisation_matches_master_equation(nthreads, mode):
     """2A -> B (c1 A(A-1)/2), B -> 2A (c2 B), A0 = 1000: A + 2B = 1000, a 501-state chain."""
     c1, c2 = 0.001, 0.1
     net = W.dimerisation(c1, c2)
     n_traj = 4000
-    o = oracle.run(net, [1000, 0], 10.0, n_traj, seed=3, sample_dt=0.1, want_grid=True, n_threads=nthreads)
+    o = _run(mode, net, [1000, 0], 10.0, n_traj, seed=3, sample_dt=0.1, want_grid=True, n_threads=nthreads)
     assert (o["grid"][:, :, 0] + 2 * o["grid"][:, :, 1] == 1000).all()
     states = list(range(501))
 
@@ -195,13 +210,14 @@ def test_dimerisation_matches_master_equation(nthreads):
         assert abs(b.mean() - mean) < 4 * sd / math.sqrt(n_traj)
 
 
-def test_small_lotka_volterra_matches_master_equation(nthreads):
+@pytest.mark.parametrize("mode", MODES)
+def test_small_lotka_volterra_matches_master_equation(nthreads, mode):
     """X -> 2X (c1), X + Y -> 2Y (c2), Y -> 0 (c3) from (10, 10), truncated CME with leak < 1e-9."""
     c1, c2, c3 = 1.0, 0.1, 1.0
     net = W.lotka_volterra(c1, c2, c3)
     n_traj = 20000
     T = 1.0
-    o = oracle.run(net, [10, 10], T, n_traj, seed=9, sample_dt=0.5, want_grid=True, n_threads=nthreads)
+    o = _run(mode, net, [10, 10], T, n_traj, seed=9, sample_dt=0.5, want_grid=True, n_threads=nthreads)
     cap = 90
     states = [(x, y) for x in range(cap + 1) for y in range(cap + 1)]
 
@@ -224,12 +240,13 @@ def test_small_lotka_volterra_matches_master_equation(nthreads):
     assert _chi2_pvalue(joint, p, min_expected=20) > 1e-4
 
 
-def test_single_step_law(nthreads):
+@pytest.mark.parametrize("mode", MODES)
+def test_single_step_law(nthreads, mode):
     """First event: waiting time ~ Exp(sum a), channel k with probability a_k / sum a, independent (Eq. 3, 23, 26)."""
     net = W.random_mass_action(5, 7, seed=101, c_sigma=0.7)
     x0 = np.array([4, 9, 2, 6, 3], np.int32)
     n_traj = 30000
-    o = oracle.run(net, x0, math.inf, n_traj, seed=2, max_events=1, trace_len=1, n_threads=nthreads)
+    o = _run(mode, net, x0, math.inf, n_traj, seed=2, max_events=1, trace_len=1, n_threads=nthreads)
     mu, dt = o["trace_mu"][:, 0], o["trace_t"][:, 0]
     S, V = net.dense_reactants(), net.dense_stoich()
     a = np.array([net.c[k] * np.prod([math.comb(int(x0[i]), int(S[k, i])) for i in range(5)]) for k in range(7)])
@@ -245,7 +262,8 @@ def test_single_step_law(nthreads):
     assert (o["x_final"] == x0 + V[mu]).all()
 
 
-def test_linear_network_mean_solves_the_rate_equation(nthreads):
+@pytest.mark.parametrize("mode", MODES)
+def test_linear_network_mean_solves_the_rate_equation(nthreads, mode):
     """First-order network: E[X(t)] solves dm/dt = J m + b exactly (matrix exponential)."""
     # 0 -> A (5), A -> B (1), B -> A (0.5), B -> 0 (0.3), A -> 0 (0.2)
     net = W._from_lists(2, [({}, {0: 1}, 5.0), ({0: 1}, {1: 1}, 1.0), ({1: 1}, {0: 1}, 0.5),
@@ -254,7 +272,7 @@ def test_linear_network_mean_solves_the_rate_equation(nthreads):
     b = np.array([5.0, 0.0])
     m0 = np.array([3.0, 7.0])
     n_traj = 20000
-    o = oracle.run(net, m0.astype(np.int32), 3.0, n_traj, seed=4, sample_dt=1.0, want_grid=True, n_threads=nthreads)
+    o = _run(mode, net, m0.astype(np.int32), 3.0, n_traj, seed=4, sample_dt=1.0, want_grid=True, n_threads=nthreads)
     aug = np.zeros((3, 3)); aug[:2, :2] = J; aug[:2, 2] = b
     for gi, t in enumerate([0.0, 1.0, 2.0, 3.0]):
         m = (scipy.linalg.expm(aug * t) @ np.append(m0, 1.0))[:2]
@@ -268,22 +286,24 @@ def test_linear_network_mean_solves_the_rate_equation(nthreads):
 # ----------------------------------------------------------------------------------
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("seed", [1, 2, 3])
-def test_state_equals_initial_plus_counts_times_stoichiometry(seed, nthreads):
+def test_state_equals_initial_plus_counts_times_stoichiometry(seed, nthreads, mode):
     """X(t) = X(0) + sum_k n_k v_k exactly (Eq. 5), for every trajectory."""
     net = W.random_mass_action(6, 12, seed=200 + seed)
     x0 = W.poisson_x0(6, 20, seed)
-    o = oracle.run(net, x0, 2.0, 200, seed=seed, max_events=20000, want_grad=True, n_threads=nthreads)
+    o = _run(mode, net, x0, 2.0, 200, seed=seed, max_events=20000, want_grad=True, n_threads=nthreads)
     V = net.dense_stoich()
     assert (o["x_final"] == x0 + o["counts"].astype(np.int64) @ V).all()
     assert (o["n_events"] == o["counts"].sum(1)).all()
 
 
-def test_grid_is_right_continuous_state_from_event_trace():
+@pytest.mark.parametrize("mode", MODES)
+def test_grid_is_right_continuous_state_from_event_trace(mode):
     """Grid value at g = X0 + sum of v_mu over events with time <= g, rebuilt from the event trace."""
     net = W.lotka_volterra()
     x0 = np.array([1000, 1000], np.int32)
-    o = oracle.run(net, x0, 0.05, 8, seed=1, sample_dt=0.001, want_grid=True, trace_len=5000)
+    o = _run(mode, net, x0, 0.05, 8, seed=1, sample_dt=0.001, want_grid=True, trace_len=5000)
     V = net.dense_stoich()
     G = o["grid"].shape[1]
     for j in range(8):
@@ -298,12 +318,13 @@ def test_grid_is_right_continuous_state_from_event_trace():
             assert (o["grid"][j, gi] == cum[m]).all()
 
 
-def test_internal_time_martingale(nthreads):
+@pytest.mark.parametrize("mode", MODES)
+def test_internal_time_martingale(nthreads, mode):
     """n_k(t) - T_k(t) is a martingale with mean 0 (random time change, Eq. 16-18)."""
     net = W.random_mass_action(4, 8, seed=77, c_sigma=0.5)
     x0 = W.poisson_x0(4, 30, 78)
     n_traj = 20000
-    o = oracle.run(net, x0, 1.0, n_traj, seed=6, want_grad=True, max_events=100000, n_threads=nthreads)
+    o = _run(mode, net, x0, 1.0, n_traj, seed=6, want_grad=True, max_events=100000, n_threads=nthreads)
     ok = o["status"] == oracle.ST_TEND
     assert ok.mean() > 0.99
     d = o["counts"][ok] - o["t_internal"][ok]
@@ -311,11 +332,12 @@ def test_internal_time_martingale(nthreads):
     assert (np.abs(d.mean(0)) < 4 * se).all()
 
 
-def test_pure_birth_likelihood_and_gradient():
+@pytest.mark.parametrize("mode", MODES)
+def test_pure_birth_likelihood_and_gradient(mode):
     """0 -> A at rate c on [0, t]: l = n ln c - c t and dl/dc = n/c - t."""
     c, T = 2.5, 3.0
     net = W.pure_birth(c)
-    o = oracle.run(net, [0], T, 50, seed=3, want_grad=True)
+    o = _run(mode, net, [0], T, 50, seed=3, want_grad=True)
     n = o["counts"][:, 0].astype(float)
     assert (o["x_final"][:, 0] == n).all()
     np.testing.assert_allclose(o["t_internal"][:, 0], c * T, rtol=1e-13)
@@ -324,12 +346,13 @@ def test_pure_birth_likelihood_and_gradient():
     np.testing.assert_allclose(g[0], (n / c - T).sum(), rtol=1e-11)
 
 
-def test_loglik_matches_path_integral_from_trace():
+@pytest.mark.parametrize("mode", MODES)
+def test_loglik_matches_path_integral_from_trace(mode):
     """l = sum over events of ln a_mu(X before) - integral of sum_k a_k(X(s)) ds, rebuilt from the trace."""
     net = W.random_mass_action(4, 6, seed=31, c_sigma=0.5)
     x0 = np.array([15, 12, 9, 20], np.int32)
     T = 0.5
-    o = oracle.run(net, x0, T, 6, seed=8, want_grad=True, trace_len=20000)
+    o = _run(mode, net, x0, T, 6, seed=8, want_grad=True, trace_len=20000)
     S, V = net.dense_reactants(), net.dense_stoich()
 
     def props(x):
@@ -370,12 +393,13 @@ def _path_loglik(net, x0, T, mu, tt, c):
     return ll - (c * ih).sum()
 
 
-def test_gradient_against_fixed_path_finite_differences():
+@pytest.mark.parametrize("mode", MODES)
+def test_gradient_against_fixed_path_finite_differences(mode):
     """d l/d c_k = (n_k - T_k(t_end)) / c_k against central differences of the recorded path's likelihood."""
     net = W.random_mass_action(3, 5, seed=55, c_sigma=0.4)
     x0 = np.array([10, 8, 12], np.int32)
     T, n_traj = 0.3, 12
-    o = oracle.run(net, x0, T, n_traj, seed=12, want_grad=True, trace_len=4000)
+    o = _run(mode, net, x0, T, n_traj, seed=12, want_grad=True, trace_len=4000)
     g = (o["counts"] - o["t_internal"]) / net.c
     for j in range(n_traj):
         n = int(o["n_events"][j])
@@ -414,21 +438,22 @@ def test_score_is_the_likelihood_ratio_derivative_under_common_random_numbers(nt
             assert abs(fd[:, i].mean() - lr[:, i].mean()) < 4 * se + 1e-9, (k, i)
 
 
-def test_absorbing_overflow_bad_x0_and_event_cap():
+@pytest.mark.parametrize("mode", MODES)
+def test_absorbing_overflow_bad_x0_and_event_cap(mode):
     """Status semantics: absorption, int32 overflow (event not fired), negative X0, max_events."""
     death = W._from_lists(1, [({0: 1}, {}, 1.0)], "death")
-    o = oracle.run(death, [5], math.inf, 3, seed=1)
+    o = _run(mode, death, [5], math.inf, 3, seed=1)
     assert (o["status"] == oracle.ST_ABSORBED).all() and (o["x_final"] == 0).all() and (o["n_events"] == 5).all()
     birth = W.pure_birth(1e6)
-    o = oracle.run(birth, [2**31 - 3], math.inf, 2, seed=1)
+    o = _run(mode, birth, [2**31 - 3], math.inf, 2, seed=1)
     assert (o["status"] == oracle.ST_OVERFLOW).all() and (o["x_final"][:, 0] == 2**31 - 1).all()
-    o = oracle.run(W.birth_death(), np.array([[-1], [3]], np.int32), 1.0, 2, seed=1, want_grad=True)
+    o = _run(mode, W.birth_death(), np.array([[-1], [3]], np.int32), 1.0, 2, seed=1, want_grad=True)
     assert o["status"].tolist() == [oracle.ST_BAD_X0, oracle.ST_TEND] and math.isnan(o["loglik"][0])
-    o = oracle.run(W.lotka_volterra(), [1000, 1000], 10.0, 2, seed=1, max_events=100)
+    o = _run(mode, W.lotka_volterra(), [1000, 1000], 10.0, 2, seed=1, max_events=100)
     assert (o["status"] == oracle.ST_MAX_EVENTS).all() and (o["n_events"] == 100).all()
-    o = oracle.run(W.lotka_volterra(), [1000, 1000], 10.0, 2, seed=1, max_events=0)
+    o = _run(mode, W.lotka_volterra(), [1000, 1000], 10.0, 2, seed=1, max_events=0)
     assert (o["status"] == oracle.ST_MAX_EVENTS).all() and (o["x_final"] == 1000).all()
-    o = oracle.run(W.lotka_volterra(), [1000, 1000], 0.0, 2, seed=1, sample_dt=0.1, want_grid=True)
+    o = _run(mode, W.lotka_volterra(), [1000, 1000], 0.0, 2, seed=1, sample_dt=0.1, want_grid=True)
     assert (o["status"] == oracle.ST_TEND).all() and o["grid"].shape == (2, 1, 2) and (o["n_events"] == 0).all()
 
 
@@ -438,3 +463,55 @@ def test_grid_length_rule():
     assert oracle.grid_len(1.0, 0.3) == 4
     assert oracle.grid_len(1.0, 0.0) == 0
     assert oracle.grid_len(math.inf, 0.1) == 0
+
+
+# ----------------------------------------------------------------------------------
+# The absolute-time form against the internal-time form, and frozen channels
+# ----------------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_lazy_form_follows_the_same_path_as_table_2(seed, nthreads):
+    """The two forms are the same method in exact arithmetic: on random uni/bimolecular networks
+    the event streams agree (channel by channel) and the times to within rounding, as long as no
+    two channels are within rounding of a tie.  A channel left stale (not touched although it
+    reads a changed species, or its internal time not brought up to the event) changes the path
+    within a few events."""
+    net = W.random_mass_action(8, 40, seed=300 + seed, c_sigma=0.8)
+    x0 = W.poisson_x0(8, 25, seed)
+    K = 400
+    e = oracle.run(net, x0, math.inf, 64, seed=seed, max_events=K, want_grad=True, trace_len=K, n_threads=nthreads)
+    z = oracle.run(net, x0, math.inf, 64, seed=seed, max_events=K, want_grad=True, trace_len=K, n_threads=nthreads,
+                   mode=oracle.MODE_LAZY)
+    same = (e["trace_mu"] == z["trace_mu"]).all(1)
+    assert same.mean() >= 0.95, same.mean()
+    assert (e["trace_mu"][:, 0] == z["trace_mu"][:, 0]).all()  # the first event is computed identically
+    assert (e["trace_t"][:, 0] == z["trace_t"][:, 0]).all()
+    np.testing.assert_allclose(z["trace_t"][same], e["trace_t"][same], rtol=1e-10, atol=0)
+    assert (z["x_final"][same] == e["x_final"][same]).all() and (z["counts"][same] == e["counts"][same]).all()
+    np.testing.assert_allclose(z["t_internal"][same], e["t_internal"][same], rtol=1e-8, atol=1e-9)
+    np.testing.assert_allclose(z["loglik"][same], e["loglik"][same], rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_forbidden_channel_is_frozen(mode, nthreads):
+    """Table 2's note: a channel forbidden to fire keeps a frozen internal time.  Birth-death with
+    its death channel forbidden is a pure birth process, A(t) ~ Poisson(k t); and forbidding a
+    channel is the same, bit for bit, as giving it rate 0."""
+    net = W.birth_death(20.0, 1.0)
+    o = _run(mode, net, [0], 2.0, 6000, seed=4, want_grad=True, enabled=[1, 0], n_threads=nthreads)
+    assert (o["counts"][:, 1] == 0).all() and (o["t_internal"][:, 1] == 0).all()
+    a = o["x_final"][:, 0]
+    assert abs(a.mean() - 40.0) < 4 * math.sqrt(40.0 / 6000)
+    assert _chi2_pvalue(np.bincount(a, minlength=120)[:120], scipy.stats.poisson.pmf(np.arange(120), 40.0)) > 1e-4
+    rnet = W.random_mass_action(5, 10, seed=41)
+    x0 = W.poisson_x0(5, 30, 42)
+    en = np.array([1, 1, 0, 1, 0, 1, 1, 1, 0, 1], np.uint8)
+    c0 = rnet.c * en
+    f = _run(mode, rnet, x0, 0.5, 20, seed=2, want_grad=True, trace_len=300, enabled=en, n_threads=nthreads)
+    z = _run(mode, rnet.with_rates(c0), x0, 0.5, 20, seed=2, want_grad=True, trace_len=300, n_threads=nthreads)
+    for k in ("x_final", "n_events", "counts", "trace_mu"):
+        assert np.array_equal(f[k], z[k]), k
+    for k in ("t_last", "t_internal", "loglik", "trace_t"):
+        assert np.array_equal(f[k].view(np.int64), z[k].view(np.int64)), k
+    assert (f["counts"][:, en == 0] == 0).all()
