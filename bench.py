@@ -1,20 +1,29 @@
-"""Benchmark: reaction events per second of the ensemble workload on GB300.
+"""Benchmark: reaction events per second on GB300, all five workloads, with rooflines.
 
-Workload (one step): the Lotka-Volterra predator-prey model of Table 4
-(c = 10, 0.01, 10; X0 = Y0 = 1000), birth-death (0 -> A at 100, A -> 0 at 1,
-A0 = 0) and dimerisation (2A -> B at 0.001, B -> 2A at 0.1, A0 = 1000), each
-2^20 trajectories to t_end = 10, one thread per trajectory, Philox seed 1,
+Headline (the line's `value`): the ensemble workload -- the Lotka-Volterra predator-prey
+model of Table 4 (c = 10, 0.01, 10; X0 = Y0 = 1000), birth-death (0 -> A at 100,
+A -> 0 at 1, A0 = 0) and dimerisation (2A -> B at 0.001, B -> 2A at 0.1, A0 = 1000),
+each 2^20 trajectories to t_end = 10, one thread per trajectory, Philox seed 1,
 ensemble moments of X on a 0.01 grid plus final states.  Step i simulates the
-trajectory ids [i * 2^20, (i+1) * 2^20) of each network.
+trajectory ids [i * 2^20, (i+1) * 2^20) of each network on rank 0 (other ranks take
+their own disjoint blocks), and the int64 moment sums are all-reduced over ranks.
 
-Printed JSON: value = events/s of the whole job (sum over ranks of fired
-events / max over ranks of the timed device time); e2e = the same metric through
-api.simulate with inputs copied from pinned host memory and outputs copied back
-inside the timed region; roofline for the dominant kernel (the Lotka-Volterra
-launch, FP64-pipe bound); cpu_baseline = the CPU oracle on the host cores over a
-bounded sample of the same workload.
+`workloads` (same JSON line, each with its own small fixed step count):
+  large   -- random network N = 1e4, M = 1e6, 16 trajectories, a bundle of blocks per
+             trajectory streaming P, T, a through HBM (HBM roofline, 32 B per
+             channel-event); --events events per trajectory per step
+  batched -- 4096 random networks, M in [4, 4096], one graph-captured persistent launch
+             (FP64-issue roofline), against one launch per network on a 512-network subset
+  grad    -- M = 64, N = 16, 65536 trajectories to t_end = 5, forward with the
+             log-likelihood + backward kernel (FP64-issue roofline), against the plain forward
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--traj N]
+Printed JSON: value = events/s of the whole job (sum over ranks of fired events / max
+over ranks of the timed device time); e2e = the same metric through api.simulate with
+inputs copied from pinned host memory and outputs copied back inside the timed region;
+roofline for the dominant kernel of each workload; cpu_baseline = the CPU oracle on
+the host cores over a bounded sample of the ensemble workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload all|ensemble|large|batched|grad]
 """
 from __future__ import annotations
 
@@ -37,42 +46,85 @@ from paper_2103_00405_gb300 import workloads as W  # noqa: E402
 METRIC = "reaction events/s on 1 GB300 (plain, batched, +grad) and % of roofline"
 UNIT = "events/s"
 SAMPLE_DT = 0.01
-# FP64 issue rate: nominal 1.25 TFLOP/s counts an FMA as 2 flops, so single adds,
-# multiplies, divides and conversions retire at most 0.625e12 per second.
-FP64_OP_PEAK = 0.625e12
-# DRAM bytes per unit of work of the roofline kernels, each from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum of one launch divided by the units it
-# processed; commands and figures in profiles/large_network_bundle_kernel.md and
-# profiles/ensemble_small_kernel_ncu.md).  Set to None when the kernel changes.
-NCU_BYTES_PER_CHANNEL_EVENT_BUNDLE = (77561792000 + 25620354048) / (200 * 16 * 1e6)
-NCU_BYTES_PER_TRAJECTORY_ENSEMBLE_LV = (830464 + 0) / 16384
+# Nominal FP64 rate: 1.25 TFLOP/s counts an FMA as 2 flops, so single adds, multiplies,
+# divides and conversions retire at most 0.625e12 per second.  The roofline peak used
+# is the rate measured by rt_fp64_probe on the same GPU at the start of the run; the
+# nominal figure is printed beside it.
+FP64_OP_NOMINAL = 0.625e12
+# DRAM bytes per unit of work of two roofline kernels, each from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch over the units it
+# processed).  A kernel changed since its capture must have its entry set to None.
+NCU_TRAFFIC = {
+    "k_bundle": dict(bytes_per_unit=(77561792000 + 25620354048) / (200 * 16 * 1e6), unit="channel-event",
+                     source="ncu capture of k_bundle<false>, N=1e4, M=1e6, 16 trajectories x 200 events"),
+    "k_ens_small": dict(bytes_per_unit=(830464 + 0) / 16384, unit="trajectory",
+                        source="ncu capture of k_ens_small<3,2,false>, 16384 Lotka-Volterra trajectories to t=10"),
+}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--traj", type=int, default=1 << 20, help="trajectories per network per step")
+    ap.add_argument("--workload", default="all", choices=["all", "ensemble", "large", "batched", "grad"],
+                    help="all (default): the ensemble headline plus the large, batched and grad sub-records; "
+                         "one name: that workload alone as the line's headline (profiling captures)")
+    ap.add_argument("--traj", type=int, default=1 << 20, help="ensemble: trajectories per network per step")
     ap.add_argument("--cpu-sample", type=int, default=1024, help="oracle trajectories per network")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--t-end", type=float, default=10.0, help="horizon (reduced only for profiling captures)")
-    ap.add_argument("--skip-e2e", action="store_true", help="omit the end-to-end leg (profiling captures)")
-    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "large", "batched", "grad"],
-                    help="ensemble (default): LV + birth-death + dimerisation; large: N=1e4, M=1e6, 16 trajectories; "
-                         "batched: 4096 uneven networks in one persistent launch; grad: M=64 forward + backward")
+    ap.add_argument("--t-end", type=float, default=10.0, help="ensemble horizon (reduced only for profiling captures)")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="ensemble: steps of the end-to-end leg (0: none)")
+    ap.add_argument("--sub-steps", type=int, default=2, help="timed steps of each workload of the `workloads` object")
+    ap.add_argument("--sub-warmup", type=int, default=1, help="warm-up steps of each workload of `workloads`")
     ap.add_argument("--batch-events", type=int, default=20_000, help="batched workload: event cap per network")
     ap.add_argument("--nets", type=int, default=4096, help="batched workload: networks (reduced only for captures)")
     ap.add_argument("--events", type=int, default=100_000, help="large workload: events per trajectory per step")
-    return ap.parse_args()
+    ap.add_argument("--grad-traj", type=int, default=65536, help="grad workload: trajectories")
+    return ap.parse_args(argv)
 
+
+# ----------------------------------------------------------------------------------------
+# Sharding and reductions over ranks (host logic; tested with gloo ranks on CPU)
+# ----------------------------------------------------------------------------------------
 
 def traj_base(rank: int, step: int, n: int) -> int:
     """First global trajectory id of a rank's step: each (rank, step) pair owns its own block of
-    n ids (steps < 1000), so ranks and steps never repeat a trajectory (weak scaling, no
-    data-path collective)."""
+    n ids (steps < 1000), so ranks and steps never repeat a trajectory (weak scaling)."""
     return (rank * 1000 + step) * n
+
+
+def shard_range(n: int, rank: int, world: int):
+    """Contiguous share [start, start + count) of n items for a rank (sizes differ by at most 1)."""
+    start = n * rank // world
+    return start, n * (rank + 1) // world - start
+
+
+def lpt_partition(costs, world: int):
+    """Longest-processing-time-first: items in decreasing cost (ties by index) go to the rank with
+    the least total cost so far (ties to the lower rank).  Returns one sorted index list per rank."""
+    order = sorted(range(len(costs)), key=lambda i: (-float(costs[i]), i))
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += float(costs[i])
+    return [sorted(p) for p in parts]
+
+
+def batched_cost(item, cap: int) -> float:
+    """Estimated work of one batched network for the partition: channels scanned per event (M)
+    times the expected events, t_end times the initial total propensity sum_k c_k h_k(X0)
+    (Eq. 1-2, with h as a product of binomials of the reactant counts), capped at `cap`."""
+    net, x = item.net, np.asarray(item.x0, np.float64)
+    h = np.ones(net.n_reactions)
+    xs = x[net.reac_sp]
+    coef = net.reac_coef
+    np.multiply.at(h, net.reac_rxn, np.where(coef == 2, xs * (xs - 1) / 2, xs))
+    events = min(float(cap), float(item.t_end) * float(np.dot(net.c, h)))
+    return float(net.n_reactions) * max(events, 1.0)
 
 
 def combine_over_ranks(ms: float, events: int, world: int, device=None):
@@ -88,6 +140,31 @@ def combine_over_ranks(ms: float, events: int, world: int, device=None):
     return t.item(), int(e.item())
 
 
+def allreduce_moments(tensors, world: int):
+    """Exact sum over ranks of int64 moment tables (grid_sum, grid_sumsq, grid_count): integer
+    addition is associative, so the result equals one process's sums over all trajectories."""
+    if world <= 1:
+        return
+    import torch.distributed as dist
+    for t in tensors:
+        dist.all_reduce(t)
+
+
+def sum_in_rank_order(t, world: int):
+    """Sum of a float64 tensor over ranks, added in rank order 0, 1, ... on every rank (the same
+    bits on every rank and in every run, unlike a reduction whose order the library picks)."""
+    if world <= 1:
+        return t.clone()
+    import torch
+    import torch.distributed as dist
+    parts = [torch.empty_like(t) for _ in range(world)]
+    dist.all_gather(parts, t.contiguous())
+    acc = parts[0].clone()
+    for p in parts[1:]:
+        acc = acc + p
+    return acc
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -96,7 +173,7 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi SM clock / throttle-reason samples during the timed region."""
+    """nvidia-smi SM clock / throttle-reason samples during a timed region."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -113,6 +190,7 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+        return self
 
     def stop(self):
         if self.proc is None:
@@ -138,20 +216,51 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def fp64_ops_per_event(net, counts):
-    """Algorithmic binary64 operations of the events (Table 2 with Eq. 17, 25):
-    per event, per channel: P-T, /a, a*dt, T+ (4); plus t+dt and P_mu+E (2); plus a
-    conversion and a multiply for every propensity the fired channel's dependency
-    list recomputes.  counts: [M] total firings per channel over the launch."""
-    S = net.dense_reactants()
-    V = net.dense_stoich()
-    M = net.n_reactions
-    changed = V != 0
-    reads = S > 0
-    deps = np.array([int((reads[:, changed[k]].any(1)).sum()) for k in range(M)])
-    n = counts.sum()
-    return float(n * (4 * M + 2) + 2 * (counts * deps).sum()), float(n)
+# ----------------------------------------------------------------------------------------
+# Roofline arithmetic
+# ----------------------------------------------------------------------------------------
 
+def dependents_per_channel(net) -> np.ndarray:
+    """For every channel k, how many propensities its firing recomputes: the channels reading a
+    species k changes, counted once per (changed species, reading channel) pair."""
+    readers = np.zeros(net.n_species, np.int64)
+    np.add.at(readers, net.reac_sp, 1)
+    deps = np.zeros(net.n_reactions, np.int64)
+    np.add.at(deps, net.stoi_rxn, readers[net.stoi_sp])
+    return deps
+
+
+def fp64_ops_per_event(net, counts):
+    """Algorithmic binary64 operations of the events (Table 2 with Eq. 17, 25): per event and
+    channel P-T, /a, a*dt, T+ (4); per event t+dt and P_mu+E (2); a conversion and a multiply
+    for every propensity the fired channel recomputes.  counts: [M] firings over the launch.
+    Returns (operations, events)."""
+    deps = dependents_per_channel(net)
+    M = net.n_reactions
+    n = float(np.sum(counts))
+    return float(n * (4 * M + 2) + 2 * float(np.dot(counts, deps))), n
+
+
+def hbm_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def alu_roofline(ops: float, launch_ms: float, fp64_peak: float, kernel: str, note: str):
+    achieved = ops / (launch_ms / 1e3)
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / fp64_peak, "frac_nominal": achieved / FP64_OP_NOMINAL, "traffic": None,
+            "kernel": kernel, "launch_ms": launch_ms, "ops_note": note,
+            "peak_note": "binary64 add/multiply issue rate measured by rt_fp64_probe in this run (of measured); "
+                         "frac_nominal: against 0.625e12 single ops/s (1.25 TFLOP/s nominal with FMA = 2)"}
+
+
+# ----------------------------------------------------------------------------------------
+# Reference arm: the CPU oracle
+# ----------------------------------------------------------------------------------------
 
 def cpu_baseline(cfgs, sample):
     import oracle
@@ -200,233 +309,73 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def hbm_peak_gbs():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["hbm_gbs"]), "measured"
-    except (OSError, KeyError, ValueError):
-        return 6800.0, "fallback"
+# ----------------------------------------------------------------------------------------
+# Timing helpers
+# ----------------------------------------------------------------------------------------
+
+class Ctx:
+    """Per-process run context: rank, world, device, stream, measured peaks."""
+
+    def __init__(self):
+        import torch
+        self.rank, self.world, self.local = dist_env()
+        torch.cuda.set_device(self.local)
+        self.dev = torch.device("cuda", self.local)
+        self.stream = torch.cuda.current_stream()
+        self.fp64_peak = None
+
+    def barrier(self):
+        import torch
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
 
 
-def run_large(args):
-    """Large-network mode: N = 1e4 species, M = 1e6 reactions, 16 trajectories, `--events` events each
-    per step (t_end = inf), a bundle of blocks per trajectory streaming P, T, a through HBM."""
+def timed_steps(ctx, step_fn, steps, warmup, before=None, after=None):
+    """Run warmup + steps calls of step_fn(i, record) bracketed by a barrier and a synchronize;
+    each timed step is measured with CUDA events on the launching stream (record(name) marks
+    named points inside the step).  before(i) / after(i) run outside the timed span of timed
+    step i (after(i) once its end event has completed).  Returns (per-step ms, marks, clocks)."""
+    import torch
+    for i in range(warmup):
+        if before:
+            before(100 + i)
+        step_fn(100 + i, lambda name: None)
+    ctx.barrier()
+    sampler = ClockSampler(ctx.local).start()
+    ms, marks = [], []
+    for i in range(steps):
+        if before:
+            before(i)
+        ev = {}
+
+        def record(name):
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(ctx.stream)
+            ev[name] = e
+        record("_start")
+        step_fn(i, record)
+        record("_end")
+        ev["_end"].synchronize()
+        ms.append(ev["_start"].elapsed_time(ev["_end"]))
+        if after:
+            after(i)
+        marks.append({k: ev["_start"].elapsed_time(v) for k, v in ev.items() if not k.startswith("_")})
+    ctx.barrier()
+    return ms, marks, sampler.stop()
+
+
+# ----------------------------------------------------------------------------------------
+# Ensemble (headline)
+# ----------------------------------------------------------------------------------------
+
+def run_ensemble(args, ctx):
     import torch
 
     from paper_2103_00405_gb300 import _lib as L
     from paper_2103_00405_gb300 import api
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    cfg = W.large_network_config(max_events=args.events)
-    net, n_traj, M = cfg["net"], cfg["n_traj"], cfg["net"].n_reactions
-    netg = api.Network(net)
-    x0 = torch.as_tensor(cfg["x0"], dtype=torch.int32).to(dev)
-    stream = torch.cuda.current_stream()
-    outs = {}
-
-    def step(i, ev=None):
-        a = b = None
-        if ev is not None:
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-        o = api.simulate(netg, x0, math.inf, n_traj, seed=1, traj_offset=traj_base(rank, i, n_traj),
-                         max_events=args.events, mapping=L.RT_MAP_BUNDLE, outputs=outs)
-        outs.update(o)
-        if ev is not None:
-            b.record(stream)
-            ev.append((a, b))
-
-    for i in range(args.warmup):
-        step(100 + i)
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
-    evts, total = [], 0
-    for i in range(args.steps):
-        step(i, evts)
-        total += int(outs["n_events"].sum().item())
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    ms = [a.elapsed_time(b) for a, b in evts]
-    dev_ms = sum(ms)
-    value = total / (dev_ms / 1e3)
-    peak, how = hbm_peak_gbs()
-    per_launch_events = total / args.steps
-    achieved = 32.0 * M * per_launch_events / (statistics.mean(ms) / 1e3) / 1e9
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "large network: random mass-action N=1e4, M=1e6 uni/bimolecular, c~lognormal(0,1), "
-                                   "X0~Poisson(100), 16 trajectories, bundle of blocks per trajectory",
-                       "events_per_trajectory_per_step": args.events, "t_end": "inf", "seed": 1,
-                       "l2": "inputs larger than L2 (16 x 24 MB of P, T, a streamed per event)"},
-            "clocks": clocks, "gpu_launches": 2 * len(evts),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak,
-                         "traffic": (NCU_BYTES_PER_CHANNEL_EVENT_BUNDLE * M * per_launch_events
-                                     if NCU_BYTES_PER_CHANNEL_EVENT_BUNDLE else None),
-                         "traffic_note": "ncu DRAM bytes of a 200-event launch, scaled to this launch's "
-                                         "channel-events", "kernel": "k_bundle",
-                         "bytes_per_channel_event": 32, "peak_source": how}}
-    if rank == 0:
-        print(json.dumps(line))
-
-
-def _timed(fn, steps, warmup, stream):
-    import torch
-    for _ in range(warmup):
-        fn()
-    torch.cuda.synchronize()
-    ms = []
-    for _ in range(steps):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        fn()
-        b.record(stream)
-        b.synchronize()
-        ms.append(a.elapsed_time(b))
-    return ms
-
-
-def run_batched(args):
-    """4096 random networks, M ~ U{4..4096}, N = max(1, M/4), c ~ lognormal(0,1), X0 ~ Poisson(50),
-    t_end ~ U[1,10], one trajectory each, capped at --batch-events events: one persistent CUDA-graph
-    launch (policy from the autotuner) against one rt_run launch per network."""
-    import torch
-
-    from paper_2103_00405_gb300 import api, autotune
-
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    items = W.batched_networks(args.nets)
-    specs = [it.net for it in items]
-    x0 = torch.from_numpy(np.concatenate([it.x0 for it in items])).to(dev)
-    t_end = torch.tensor([it.t_end for it in items], dtype=torch.float64, device=dev)
-    cap = args.batch_events
-    policy = autotune.tune_batch(specs, x0, t_end, 1, probe_events=max(100, cap // 20))
-    batch = api.Batch(specs, **policy)
-    graph, out = batch.capture(x0, t_end, 1, seed=1, max_events=cap)
-    stream = torch.cuda.current_stream()
-    sampler = ClockSampler(local)
-    sampler.start()
-    ms = _timed(graph.replay, args.steps, args.warmup, stream)
-    clocks = sampler.stop()
-    events = int(out["n_events"].sum().item())
-    value = events / (statistics.mean(ms) / 1e3)
-    # a 512-network subset both ways: one batch launch, and one rt_run launch per network
-    # (stream_id = network index in the subset, so the trajectories are identical), the
-    # per-network launches spread over 8 CUDA streams
-    sub = items[:512]
-    sbatch = api.Batch([it.net for it in sub], **policy)
-    sx0 = torch.from_numpy(np.concatenate([it.x0 for it in sub])).to(dev)
-    st = torch.tensor([it.t_end for it in sub], dtype=torch.float64, device=dev)
-    sgraph, sout = sbatch.capture(sx0, st, 1, seed=1, max_events=cap)
-    ms_sub = _timed(sgraph.replay, args.steps, 1, stream)
-    nets = [api.Network(it.net) for it in sub]
-    x0s = [torch.as_tensor(it.x0, dtype=torch.int32).to(dev) for it in sub]
-    outs = [{} for _ in sub]
-    streams = [torch.cuda.Stream() for _ in range(8)]
-
-    def per_network():
-        for s_ in streams:
-            s_.wait_stream(stream)
-        for i, it in enumerate(sub):
-            with torch.cuda.stream(streams[i % 8]):
-                api.simulate(nets[i], x0s[i], it.t_end, 1, seed=1, stream_id=i, max_events=cap, outputs=outs[i])
-        for s_ in streams:
-            stream.wait_stream(s_)
-
-    ms_plain = _timed(per_network, 1, 1, stream)
-    plain_events = sum(int(o["n_events"].sum().item()) for o in outs)
-    sub_events = int(sout["n_events"].sum().item())
-    assert plain_events == sub_events, (plain_events, sub_events)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "batched: %d random networks, M~U{4..4096}, N=M/4, c~lognormal(0,1), "
-                                   "X0~Poisson(50), t_end~U[1,10], 1 trajectory each, one persistent graph launch"
-                                   % args.nets,
-                       "max_events_per_network": cap, "policy": policy, "events_per_step": events},
-            "clocks": clocks, "gpu_launches": len(ms),
-            "subset_512": {"batched_events_per_s": sub_events / (statistics.mean(ms_sub) / 1e3),
-                           "per_network_launches_events_per_s": plain_events / (statistics.mean(ms_plain) / 1e3),
-                           "unit": UNIT, "events": sub_events, "per_network_streams": 8}}
-    if rank == 0:
-        print(json.dumps(line))
-
-
-def run_grad(args):
-    """Random network M = 64, N = 16, c ~ lognormal(0, 0.5), X0 ~ Poisson(200), 65536 trajectories to
-    t_end = 5: forward with log-likelihood plus the backward kernel, against the plain forward."""
-    import torch
-
-    from paper_2103_00405_gb300 import api
-
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    cfg = W.grad_config()
-    net, n = cfg["net"], cfg["n_traj"]
-    c = torch.tensor(net.c, dtype=torch.float64, requires_grad=True)
-    netg = api.Network(net)
-    x0 = torch.as_tensor(cfg["x0"], dtype=torch.int32).to(dev)
-    out_plain, out_grad = {}, {}
-    stream = torch.cuda.current_stream()
-    state = {}
-
-    def fwd_bwd():
-        o = api.simulate(netg, x0, cfg["t_end"], n, seed=1, max_events=10**8, grad=True, outputs=out_grad)
-        state["g"] = api.loglik_backward(netg, torch.ones(n, dtype=torch.float64, device=dev), o["counts"],
-                                         o["t_internal"])
-
-    def fwd_plain():
-        api.simulate(netg, x0, cfg["t_end"], n, seed=1, max_events=10**8, outputs=out_plain)
-
-    sampler = ClockSampler(local)
-    sampler.start()
-    ms = _timed(fwd_bwd, args.steps, args.warmup, stream)
-    clocks = sampler.stop()
-    ms_plain = _timed(fwd_plain, args.steps, args.warmup, stream)
-    events = int(out_grad["n_events"].sum().item())
-    assert events == int(out_plain["n_events"].sum().item())
-    line = {"metric": METRIC, "value": events / (statistics.mean(ms) / 1e3), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "gradient: random network M=64, N=16, c~lognormal(0,0.5), X0~Poisson(200), "
-                                   "65536 trajectories to t_end=5, forward with log-likelihood + backward kernel",
-                       "events_per_step": events},
-            "clocks": clocks, "gpu_launches": 2 * len(ms),
-            "plain_forward": {"value": events / (statistics.mean(ms_plain) / 1e3), "unit": UNIT,
-                              "ms_per_step": statistics.mean(ms_plain)}}
-    if rank == 0:
-        print(json.dumps(line))
-
-
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload == "large":
-        return run_large(args)
-    if args.workload == "batched":
-        return run_batched(args)
-    if args.workload == "grad":
-        return run_grad(args)
-
-    import torch
-
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    from paper_2103_00405_gb300 import _lib as L
-    from paper_2103_00405_gb300 import api
-
-    dev = torch.device("cuda", local)
     n = args.traj
     cfgs = W.ensemble_configs(n)
     for c in cfgs:
@@ -436,69 +385,52 @@ def main():
     outs = []
     for c in cfgs:
         N = c["net"].n_species
-        outs.append(dict(x_final=torch.empty((n, N), dtype=torch.int32, device=dev),
-                         n_events=torch.empty(n, dtype=torch.int64, device=dev),
-                         status=torch.empty(n, dtype=torch.int32, device=dev),
-                         t_last=torch.empty(n, dtype=torch.float64, device=dev),
-                         grid_sum=torch.zeros((G, N), dtype=torch.int64, device=dev),
-                         grid_sumsq=torch.zeros((G, N), dtype=torch.int64, device=dev),
-                         grid_count=torch.zeros(G, dtype=torch.int64, device=dev)))
-    x0s = [torch.as_tensor(c["x0"], dtype=torch.int32).to(dev) for c in cfgs]
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
-    stream = torch.cuda.current_stream()
+        outs.append(dict(x_final=torch.empty((n, N), dtype=torch.int32, device=ctx.dev),
+                         n_events=torch.empty(n, dtype=torch.int64, device=ctx.dev),
+                         status=torch.empty(n, dtype=torch.int32, device=ctx.dev),
+                         t_last=torch.empty(n, dtype=torch.float64, device=ctx.dev),
+                         grid_sum=torch.zeros((G, N), dtype=torch.int64, device=ctx.dev),
+                         grid_sumsq=torch.zeros((G, N), dtype=torch.int64, device=ctx.dev),
+                         grid_count=torch.zeros(G, dtype=torch.int64, device=ctx.dev)))
+    x0s = [torch.as_tensor(c["x0"], dtype=torch.int32).to(ctx.dev) for c in cfgs]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=ctx.dev)  # > L2 (129 MB)
+    moments = [o[k] for o in outs for k in ("grid_sum", "grid_sumsq", "grid_count")]
 
-    def step(i, timed_events=None):
-        base = traj_base(rank, i, n)
+    def before(i):
+        flush.fill_(i & 0xFF)  # evict L2 between timed steps (outside the timed span)
+        for t in moments:
+            t.zero_()
+
+    def step(i, record):
+        base = traj_base(ctx.rank, i, n)
         for k, c in enumerate(cfgs):
-            for key in ("grid_sum", "grid_sumsq", "grid_count"):
-                outs[k][key].zero_()
-            e0 = e1 = None
-            if timed_events is not None:
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
             api.simulate(nets[k], x0s[k], c["t_end"], n, seed=c["seed"], traj_offset=base, sample_dt=SAMPLE_DT,
                          max_events=c["max_events"], grid="moments", mapping=L.RT_MAP_THREAD, outputs=outs[k])
-            if timed_events is not None:
-                e1.record(stream)
-                timed_events.append((k, e0, e1))
+            record("launch%d" % k)
+        allreduce_moments(moments, ctx.world)  # the ensemble's one exchange: exact int64 sums
 
-    for i in range(args.warmup):
-        step(100 + i)
-    torch.cuda.synchronize()
-
-    sampler = ClockSampler(local)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    evts = []
-    total_events = 0
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)  # evict L2 between timed steps (not inside the timed spans)
-        step(i, evts)
-        total_events += sum(int(o["n_events"].sum().item()) for o in outs)
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    per_launch = [(k, a.elapsed_time(b)) for k, a, b in evts]
-    dev_ms = sum(ms for _, ms in per_launch)
-    dev_ms, total_events = combine_over_ranks(dev_ms, total_events, world, dev)
+    step_events = []
+    ms, marks, clocks = timed_steps(ctx, step, args.steps, args.warmup, before,
+                                    after=lambda i: step_events.append(
+                                        sum(int(o["n_events"].sum().item()) for o in outs)))
+    dev_ms, total_events = combine_over_ranks(sum(ms), sum(step_events), ctx.world, ctx.dev)
     value = total_events / (dev_ms / 1e3)
 
-    # dominant kernel: the Lotka-Volterra launch; its algorithmic FP64 ops from the firing counts
-    lv_ms = [ms for k, ms in per_launch if k == 0]
-    lv_launch_ms = statistics.mean(lv_ms)
-    netc = api.Network(cfgs[0]["net"])
-    # firing mix of the last timed Lotka-Volterra launch from its first n/16 trajectories (same ids)
-    chk = api.simulate(netc, x0s[0], args.t_end, max(1, n // 16), seed=1,
-                       traj_offset=traj_base(rank, args.steps - 1, n), grad=True, mapping=L.RT_MAP_THREAD,
+    # dominant kernel: the Lotka-Volterra launch (launch0 of each step); its algorithmic FP64
+    # operations from the firing mix of the last step's first n/16 trajectories (same ids)
+    lv_ms = [m["launch0"] for m in marks]
+    chk = api.simulate(api.Network(cfgs[0]["net"]), x0s[0], args.t_end, max(1, n // 16), seed=1,
+                       traj_offset=traj_base(ctx.rank, args.steps - 1, n), grad=True, mapping=L.RT_MAP_THREAD,
                        max_events=cfgs[0]["max_events"])
     counts = chk["counts"].sum(0, dtype=torch.int64).cpu().numpy()
     ops_s, ev_s = fp64_ops_per_event(cfgs[0]["net"], counts)
-    lv_last_events = int(outs[0]["n_events"].sum().item())
-    ops = ops_s / ev_s * lv_last_events
-    lv_events = lv_last_events
-    achieved = ops / (lv_ms[-1] / 1e3) / 1e12
+    lv_events = int(outs[0]["n_events"].sum().item())
+    roof = alu_roofline(ops_s / ev_s * lv_events, lv_ms[-1], ctx.fp64_peak, "k_ens_small<3,2,false> "
+                        "(Lotka-Volterra launch)", "%.3f algorithmic FP64 ops per event (4M+2 + 2 per recomputed "
+                        "propensity)" % (ops_s / ev_s))
+    tr = NCU_TRAFFIC["k_ens_small"]
+    roof["traffic"] = tr["bytes_per_unit"] * n if tr["bytes_per_unit"] else None
+    roof["traffic_note"] = tr["source"] + ", scaled to this launch's trajectories"
 
     # end to end through the public API: pinned host inputs in, results back to pinned host memory
     x0_host = [torch.as_tensor(c["x0"], dtype=torch.int32).pin_memory() for c in cfgs]
@@ -508,57 +440,286 @@ def main():
     h2d = sum(x.numel() * x.element_size() for x in x0_host)
     d2h = sum(v.numel() * v.element_size() for ho in host_out for v in ho.values())
     e2e_ms, e2e_events = 0.0, 0
-    for i in range(0 if args.skip_e2e else args.steps):
+    for i in range(min(args.e2e_steps, args.steps)):
         flush.fill_(i & 0xFF)
-        torch.cuda.synchronize()
+        for t in moments:
+            t.zero_()
+        ctx.barrier()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
+        a.record(ctx.stream)
         for k, c in enumerate(cfgs):
-            xd = x0_host[k].to(dev, non_blocking=True)
-            for key in ("grid_sum", "grid_sumsq", "grid_count"):
-                outs[k][key].zero_()
-            api.simulate(nets[k], xd, c["t_end"], n, seed=c["seed"], traj_offset=traj_base(rank, 50 + i, n),
+            xd = x0_host[k].to(ctx.dev, non_blocking=True)
+            api.simulate(nets[k], xd, c["t_end"], n, seed=c["seed"], traj_offset=traj_base(ctx.rank, 50 + i, n),
                          sample_dt=SAMPLE_DT, max_events=c["max_events"], grid="moments", mapping=L.RT_MAP_THREAD,
                          outputs=outs[k])
+        allreduce_moments(moments, ctx.world)
+        for k in range(len(cfgs)):
             for key, hv in host_out[k].items():
                 hv.copy_(outs[k][key], non_blocking=True)
-        b.record(stream)
+        b.record(ctx.stream)
         b.synchronize()
         e2e_ms += a.elapsed_time(b)
         e2e_events += sum(int(ho["n_events"].sum()) for ho in host_out)
     if e2e_ms > 0:
-        e2e_ms, e2e_events = combine_over_ranks(e2e_ms, e2e_events, world, dev)
+        e2e_ms, e2e_events = combine_over_ranks(e2e_ms, e2e_events, ctx.world, ctx.dev)
     e2e_value = e2e_events / (e2e_ms / 1e3) if e2e_ms > 0 else None
 
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": ENSEMBLE_WORKLOAD,
-                       "trajectories_per_network": n, "t_end": args.t_end, "sample_dt": SAMPLE_DT, "seed": 1,
-                       "max_events_per_trajectory": cfgs[0]["max_events"],
-                       "parallelism": "trajectories sharded over ranks" if world > 1 else "1 GPU",
-                       "l2": "flushed between timed steps (512 MB write)",
-                       "events_per_step": total_events / args.steps},
-            "clocks": clocks,
-            "gpu_launches": len(evts),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_OP_PEAK / 1e12, "unit": "TFLOP/s",
-                         "frac": achieved * 1e12 / FP64_OP_PEAK,
-                         "traffic": (NCU_BYTES_PER_TRAJECTORY_ENSEMBLE_LV * n
-                                     if NCU_BYTES_PER_TRAJECTORY_ENSEMBLE_LV else None),
-                         "traffic_note": "ncu DRAM bytes of a 16384-trajectory launch to t_end=10, scaled to "
-                                         "this launch's trajectories",
-                         "kernel": "k_ens_small (Lotka-Volterra launch)", "launch_ms": lv_ms[-1],
-                         "fp64_ops_per_event": ops / lv_events,
-                         "peak_note": "FP64 pipe: nominal 1.25 TFLOP/s with FMA=2 -> 0.625e12 single ops/s (fallback)"},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        }
-        if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(cfgs, args.cpu_sample)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ctx.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": ENSEMBLE_WORKLOAD, "trajectories_per_network": n, "t_end": args.t_end,
+                   "sample_dt": SAMPLE_DT, "seed": 1, "max_events_per_trajectory": cfgs[0]["max_events"],
+                   "parallelism": ("trajectories sharded over %d ranks, int64 moment sums all-reduced"
+                                   % ctx.world) if ctx.world > 1 else "1 GPU",
+                   "l2": "flushed between timed steps (512 MB write)",
+                   "events_per_step": total_events / args.steps},
+        "clocks": clocks,
+        "gpu_launches": 3 * args.steps,
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": min(args.e2e_steps, args.steps)},
+    }
+    if not args.no_cpu_baseline and ctx.world == 1:
+        line["cpu_baseline"] = cpu_baseline(cfgs, args.cpu_sample)
+    return line
+
+
+# ----------------------------------------------------------------------------------------
+# Large network (eager bundle)
+# ----------------------------------------------------------------------------------------
+
+def run_large(args, ctx, steps, warmup):
+    """N = 1e4 species, M = 1e6 reactions, 16 trajectories per rank (replicas: a single
+    trajectory does not shard), `--events` events each per step from a fresh start (t_end = inf),
+    a bundle of blocks per trajectory streaming P, T, a through HBM."""
+    import torch
+
+    from paper_2103_00405_gb300 import _lib as L
+    from paper_2103_00405_gb300 import api
+
+    cfg = W.large_network_config(max_events=args.events)
+    net, n_traj, M = cfg["net"], cfg["n_traj"], cfg["net"].n_reactions
+    netg = api.Network(net)
+    x0 = torch.as_tensor(cfg["x0"], dtype=torch.int32).to(ctx.dev)
+    outs = {}
+    step_events = []
+
+    def step(i, record):
+        o = api.simulate(netg, x0, math.inf, n_traj, seed=1, traj_offset=traj_base(ctx.rank, i, n_traj),
+                         max_events=args.events, mapping=L.RT_MAP_BUNDLE, outputs=outs)
+        outs.update(o)
+
+    ms, _, clocks = timed_steps(ctx, step, steps, warmup,
+                                after=lambda i: step_events.append(int(outs["n_events"].sum().item())))
+    events = sum(step_events)
+    dev_ms, events_all = combine_over_ranks(sum(ms), events, ctx.world, ctx.dev)
+    peak, how = hbm_peak_gbs()
+    per_launch_events = events / steps
+    achieved = 32.0 * M * per_launch_events / (statistics.mean(ms) / 1e3) / 1e9
+    tr = NCU_TRAFFIC["k_bundle"]
+    return {"value": events_all / (dev_ms / 1e3), "unit": UNIT, "steps": steps, "warmup": warmup,
+            "ms_per_step": dev_ms / steps,
+            "config": {"workload": "large network: random mass-action N=1e4, M=1e6 uni/bimolecular, "
+                                   "c~lognormal(0,1), X0~Poisson(100), 16 trajectories per rank, bundle of blocks "
+                                   "per trajectory",
+                       "events_per_trajectory_per_step": args.events,
+                       "step": "16 fresh trajectories (new ids each step, init kernel inside the timed span) "
+                               "run for %d events each; the 1e6-event runs of the configuration take 10 such "
+                               "steps" % args.events,
+                       "t_end": "inf", "seed": 1, "parallelism": "replicas" if ctx.world > 1 else "1 GPU",
+                       "l2": "inputs larger than L2 (16 x 24 MB of P, T, a streamed per event)"},
+            "events_per_step": events_all / steps, "clocks": clocks, "gpu_launches": 2 * steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": (tr["bytes_per_unit"] * M * per_launch_events if tr["bytes_per_unit"] else None),
+                         "traffic_note": tr["source"] + ", scaled to this launch's channel-events",
+                         "kernel": "k_bundle<false>", "bytes_per_channel_event": 32, "peak_source": how}}
+
+
+# ----------------------------------------------------------------------------------------
+# Batched
+# ----------------------------------------------------------------------------------------
+
+def run_batched(args, ctx, steps, warmup):
+    """4096 random networks, M ~ U{4..4096}, N = max(1, M/4), c ~ lognormal(0,1), X0 ~ Poisson(50),
+    t_end ~ U[1,10], one trajectory each, capped at --batch-events events: one persistent CUDA-graph
+    launch (policy from the autotuner) per rank over its longest-processing-time-first share of the
+    networks, against one rt_run launch per network on a 512-network subset."""
+    import torch
+
+    from paper_2103_00405_gb300 import api, autotune
+
+    items_all = W.batched_networks(args.nets)
+    mine = lpt_partition([batched_cost(it, args.batch_events) for it in items_all], ctx.world)[ctx.rank]
+    items = [items_all[i] for i in mine]
+    specs = [it.net for it in items]
+    sid = np.asarray(mine, np.uint32)  # each network keeps its global Philox stream
+    x0 = torch.from_numpy(np.concatenate([it.x0 for it in items])).to(ctx.dev)
+    t_end = torch.tensor([it.t_end for it in items], dtype=torch.float64, device=ctx.dev)
+    cap = args.batch_events
+    policy = autotune.tune_batch(specs, x0, t_end, 1, probe_events=max(100, cap // 20))
+    batch = api.Batch(specs, stream_ids=sid, **policy)
+    graph, out = batch.capture(x0, t_end, 1, seed=1, max_events=cap)
+    ms, _, clocks = timed_steps(ctx, lambda i, r: graph.replay(), steps, warmup)
+    ev_net = out["n_events"][:, 0].cpu().numpy()
+    events = int(ev_net.sum())
+    dev_ms, events_all = combine_over_ranks(sum(ms), events * steps, ctx.world, ctx.dev)
+
+    # algorithmic FP64 operations: per event of network i, 4 M_i + 2, plus 2 per recomputed
+    # propensity with the mean dependents count of the network's channels
+    ops = 0.0
+    for it, e in zip(items, ev_net):
+        ops += float(e) * (4 * it.net.n_reactions + 2 + 2 * float(dependents_per_channel(it.net).mean()))
+    roof = alu_roofline(ops, statistics.mean(ms), ctx.fp64_peak, "k_batch<false> (persistent, graph-captured)",
+                        "per event of network i: 4 M_i + 2 + 2 x mean dependents of its channels")
+
+    line = {"value": events_all / (dev_ms / 1e3), "unit": UNIT, "steps": steps, "warmup": warmup,
+            "ms_per_step": dev_ms / steps,
+            "config": {"workload": "batched: %d random networks, M~U{4..4096}, N=M/4, c~lognormal(0,1), "
+                                   "X0~Poisson(50), t_end~U[1,10], 1 trajectory each, one persistent graph launch"
+                                   % args.nets, "max_events_per_network": cap, "policy": policy,
+                       "networks_this_rank": len(items),
+                       "parallelism": ("networks split over %d ranks, longest processing time first"
+                                       % ctx.world) if ctx.world > 1 else "1 GPU",
+                       "l2": "network arena ~%d MB re-read from L2/HBM; graph replays back to back"
+                             % int(sum(it.net.n_reactions for it in items) * 40 / 2**20)},
+            "events_per_step": events_all / steps, "clocks": clocks, "gpu_launches": steps, "roofline": roof}
+
+    if ctx.rank == 0:
+        # a 512-network subset both ways: one batch launch, and one rt_run launch per network
+        # (stream_id = the network's id, so the trajectories are identical), spread over 8 streams
+        sub_idx = mine[:512]
+        sub = [items_all[i] for i in sub_idx]
+        sbatch = api.Batch([it.net for it in sub], stream_ids=np.asarray(sub_idx, np.uint32), **policy)
+        sx0 = torch.from_numpy(np.concatenate([it.x0 for it in sub])).to(ctx.dev)
+        st = torch.tensor([it.t_end for it in sub], dtype=torch.float64, device=ctx.dev)
+        sgraph, sout = sbatch.capture(sx0, st, 1, seed=1, max_events=cap)
+        ms_sub, _, _ = timed_steps(_Solo(ctx), lambda i, r: sgraph.replay(), steps, 1)
+        nets = [api.Network(it.net) for it in sub]
+        x0s = [torch.as_tensor(it.x0, dtype=torch.int32).to(ctx.dev) for it in sub]
+        outs = [{} for _ in sub]
+        streams = [torch.cuda.Stream() for _ in range(8)]
+
+        def per_network(i, r):
+            for s_ in streams:
+                s_.wait_stream(ctx.stream)
+            for q, it in enumerate(sub):
+                with torch.cuda.stream(streams[q % 8]):
+                    api.simulate(nets[q], x0s[q], it.t_end, 1, seed=1, stream_id=int(sub_idx[q]), max_events=cap,
+                                 outputs=outs[q])
+            for s_ in streams:
+                ctx.stream.wait_stream(s_)
+
+        ms_plain, _, _ = timed_steps(_Solo(ctx), per_network, 1, 1)
+        plain_events = sum(int(o["n_events"].sum().item()) for o in outs)
+        sub_events = int(sout["n_events"].sum().item())
+        assert plain_events == sub_events, (plain_events, sub_events)
+        line["subset_512"] = {"batched_events_per_s": sub_events / (statistics.mean(ms_sub) / 1e3),
+                              "per_network_launches_events_per_s": plain_events / (statistics.mean(ms_plain) / 1e3),
+                              "unit": UNIT, "events": sub_events, "per_network_streams": 8}
+    return line
+
+
+class _Solo:
+    """A single-rank view of a context (for comparisons that only rank 0 runs)."""
+
+    def __init__(self, ctx):
+        self.rank, self.world, self.local = 0, 1, ctx.local
+        self.dev, self.stream = ctx.dev, ctx.stream
+
+    def barrier(self):
+        import torch
+        torch.cuda.synchronize()
+
+
+# ----------------------------------------------------------------------------------------
+# Gradient
+# ----------------------------------------------------------------------------------------
+
+def run_grad(args, ctx, steps, warmup):
+    """Random network M = 64, N = 16, c ~ lognormal(0, 0.5), X0 ~ Poisson(200), 65536 trajectories
+    to t_end = 5 (sharded over ranks by global id): forward with the log-likelihood plus the
+    backward kernel, grad_c summed over ranks in rank order; against the plain forward."""
+    import torch
+
+    from paper_2103_00405_gb300 import api
+
+    cfg = W.grad_config(args.grad_traj)
+    net = cfg["net"]
+    start, n = shard_range(cfg["n_traj"], ctx.rank, ctx.world)
+    netg = api.Network(net)
+    x0 = torch.as_tensor(cfg["x0"], dtype=torch.int32).to(ctx.dev)
+    out_plain, out_grad = {}, {}
+    ones = torch.ones(n, dtype=torch.float64, device=ctx.dev)
+    state = {}
+
+    def fwd_bwd(i, record):
+        o = api.simulate(netg, x0, cfg["t_end"], n, seed=1, traj_offset=start, max_events=10**8, grad=True,
+                         outputs=out_grad)
+        record("forward")
+        g = api.loglik_backward(netg, ones, o["counts"], o["t_internal"])
+        state["g"] = sum_in_rank_order(g, ctx.world)
+
+    def fwd_plain(i, record):
+        api.simulate(netg, x0, cfg["t_end"], n, seed=1, traj_offset=start, max_events=10**8, outputs=out_plain)
+
+    ms, marks, clocks = timed_steps(ctx, fwd_bwd, steps, warmup)
+    ms_plain, _, _ = timed_steps(ctx, fwd_plain, steps, warmup)
+    events = int(out_grad["n_events"].sum().item())
+    assert events == int(out_plain["n_events"].sum().item())
+    dev_ms, events_all = combine_over_ranks(sum(ms), events * steps, ctx.world, ctx.dev)
+    pms, _ = combine_over_ranks(sum(ms_plain), 0, ctx.world, ctx.dev)
+    counts = out_grad["counts"].sum(0, dtype=torch.int64).cpu().numpy()
+    ops, ev = fp64_ops_per_event(net, counts)
+    fwd_ms = statistics.mean(m["forward"] for m in marks)
+    roof = alu_roofline(ops, fwd_ms, ctx.fp64_peak, "k_ens_warp<2,true> (forward with the log-likelihood)",
+                        "%.1f algorithmic FP64 ops per event (4M+2 + 2 per recomputed propensity; the "
+                        "fixed-point logarithms are integer work)" % (ops / ev))
+    return {"value": events_all / (dev_ms / 1e3), "unit": UNIT, "steps": steps, "warmup": warmup,
+            "ms_per_step": dev_ms / steps,
+            "config": {"workload": "gradient: random network M=64, N=16, c~lognormal(0,0.5), X0~Poisson(200), "
+                                   "%d trajectories to t_end=5, forward with log-likelihood + backward kernel"
+                                   % cfg["n_traj"],
+                       "parallelism": ("trajectories sharded over %d ranks, grad_c summed in rank order"
+                                       % ctx.world) if ctx.world > 1 else "1 GPU",
+                       "l2": "state in registers; outputs 64 MB written per step"},
+            "events_per_step": events_all / steps, "clocks": clocks, "gpu_launches": 2 * steps,
+            "backward_ms": statistics.mean(m_ - m["forward"] for m_, m in zip(ms, marks)),
+            "roofline": roof,
+            "plain_forward": {"value": events_all / (pms / 1e3), "unit": UNIT, "ms_per_step": pms / steps}}
+
+
+# ----------------------------------------------------------------------------------------
+
+def main(argv=None):
+    args = parse(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    ctx = Ctx()
+    if ctx.world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2103_00405_gb300 import api
+    ctx.fp64_peak = api.fp64_probe()
+    sub = dict(steps=args.sub_steps, warmup=args.sub_warmup)
+    if args.workload in ("all", "ensemble"):
+        line = run_ensemble(args, ctx)
+        if args.workload == "all":
+            line["workloads"] = {"large": run_large(args, ctx, **sub), "batched": run_batched(args, ctx, **sub),
+                                 "grad": run_grad(args, ctx, **sub)}
+    else:
+        fn = {"large": run_large, "batched": run_batched, "grad": run_grad}[args.workload]
+        rec = fn(args, ctx, args.steps, args.warmup)
+        line = {"metric": METRIC, "value": rec.pop("value"), "unit": UNIT, "n_gpus": ctx.world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": rec.pop("ms_per_step"), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic"}
+        line.update(rec)
+    line["fp64_peak_ops_per_s"] = ctx.fp64_peak
+    if ctx.rank == 0:
         print(json.dumps(line))
-    if world > 1:
+    if ctx.world > 1:
         torch.distributed.destroy_process_group()
 
 
