@@ -12,6 +12,8 @@ their own disjoint blocks), and the int64 moment sums are all-reduced over ranks
   large   -- random network N = 1e4, M = 1e6, 16 trajectories, a bundle of blocks per
              trajectory streaming P, T, a through HBM (HBM roofline, 32 B per
              channel-event); --events events per trajectory per step
+  large_tree -- the same network as configured (16 trajectories x 1e6 events) in the
+             absolute-time form: a thread-block cluster per trajectory, min-tree argmin
   batched -- 4096 random networks, M in [4, 4096], one graph-captured persistent launch
              (FP64-issue roofline), against one launch per network on a 512-network subset
   grad    -- M = 64, N = 16, 65536 trajectories to t_end = 5, forward with the
@@ -68,7 +70,7 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="all", choices=["all", "ensemble", "large", "batched", "grad"],
+    ap.add_argument("--workload", default="all", choices=["all", "ensemble", "large", "large_tree", "batched", "grad"],
                     help="all (default): the ensemble headline plus the large, batched and grad sub-records; "
                          "one name: that workload alone as the line's headline (profiling captures)")
     ap.add_argument("--traj", type=int, default=1 << 20, help="ensemble: trajectories per network per step")
@@ -81,6 +83,8 @@ def parse(argv=None):
     ap.add_argument("--batch-events", type=int, default=20_000, help="batched workload: event cap per network")
     ap.add_argument("--nets", type=int, default=4096, help="batched workload: networks (reduced only for captures)")
     ap.add_argument("--events", type=int, default=100_000, help="large workload: events per trajectory per step")
+    ap.add_argument("--tree-events", type=int, default=1_000_000,
+                    help="large_tree workload: events per trajectory per step (the configuration's 1e6)")
     ap.add_argument("--grad-traj", type=int, default=65536, help="grad workload: trajectories")
     return ap.parse_args(argv)
 
@@ -537,6 +541,78 @@ def run_large(args, ctx, steps, warmup):
                          "kernel": "k_bundle<false>", "bytes_per_channel_event": 32, "peak_source": how}}
 
 
+def distinct_dependents(net, channels) -> np.ndarray:
+    """For each listed channel k, how many distinct channels (k itself included) its firing touches
+    in the absolute-time form: k and every channel reading a species k changes."""
+    order = np.argsort(net.reac_sp, kind="stable")
+    rsp, rk = net.reac_sp[order], net.reac_rxn[order]
+    start = np.searchsorted(rsp, np.arange(net.n_species + 1))
+    vord = np.argsort(net.stoi_rxn, kind="stable")
+    vk, vsp = net.stoi_rxn[vord], net.stoi_sp[vord]
+    vstart = np.searchsorted(vk, np.arange(net.n_reactions + 1))
+    out = []
+    for k in np.asarray(channels).tolist():
+        touched = {k}
+        for sp in vsp[vstart[k]:vstart[k + 1]].tolist():
+            touched.update(rk[start[sp]:start[sp + 1]].tolist())
+        out.append(len(touched))
+    return np.array(out, np.int64)
+
+
+def run_large_tree(args, ctx, steps, warmup):
+    """The large-network configuration as written -- N = 1e4, M = 1e6, 16 trajectories per rank,
+    1e6 events each (t_end = inf) -- in the absolute-time form on the tree mapping: a cluster of
+    CTAs per trajectory, min-tree argmin, only the channels an event touches updated."""
+    import torch
+
+    from paper_2103_00405_gb300 import _lib as L
+    from paper_2103_00405_gb300 import api
+
+    ev_per_traj = args.tree_events
+    cfg = W.large_network_config(max_events=ev_per_traj)
+    net, n_traj = cfg["net"], cfg["n_traj"]
+    netg = api.Network(net)
+    x0 = torch.as_tensor(cfg["x0"], dtype=torch.int32).to(ctx.dev)
+    outs = {}
+    step_events = []
+
+    def step(i, record):
+        outs.update(api.simulate(netg, x0, math.inf, n_traj, seed=1, traj_offset=traj_base(ctx.rank, i, n_traj),
+                                 max_events=ev_per_traj, form=L.RT_FORM_ABSOLUTE, outputs=outs))
+
+    ms, _, clocks = timed_steps(ctx, step, steps, warmup,
+                                after=lambda i: step_events.append(int(outs["n_events"].sum().item())))
+    events = sum(step_events)
+    dev_ms, events_all = combine_over_ranks(sum(ms), events, ctx.world, ctx.dev)
+    # algorithmic bytes per event: per touched channel its 32-byte record read and written, its
+    # firing time written (8), its reader-list entry, reactant descriptor and rate read (4 + 8 + 8);
+    # per touched 32-channel group the group's firing times re-read (256)
+    chk = api.simulate(netg, x0, math.inf, 1, seed=1, traj_offset=traj_base(ctx.rank, steps - 1, n_traj),
+                       max_events=min(ev_per_traj, 20000), grad=True, form=L.RT_FORM_ABSOLUTE)
+    counts = chk["counts"][0].cpu().numpy().astype(np.float64)
+    fired = np.flatnonzero(counts)
+    touched = float(np.dot(counts[fired], distinct_dependents(net, fired)) / max(1.0, counts.sum()))
+    bytes_per_event = touched * (32 + 32 + 8 + 4 + 8 + 8 + 256)
+    peak, how = hbm_peak_gbs()
+    achieved = bytes_per_event * (events / steps) / (statistics.mean(ms) / 1e3) / 1e9
+    return {"value": events_all / (dev_ms / 1e3), "unit": UNIT, "steps": steps, "warmup": warmup,
+            "ms_per_step": dev_ms / steps,
+            "config": {"workload": "large network as configured: random mass-action N=1e4, M=1e6 uni/bimolecular, "
+                                   "c~lognormal(0,1), X0~Poisson(100), 16 trajectories x %d events each per rank, "
+                                   "absolute-time form (dependency graph), a thread-block cluster per trajectory, "
+                                   "min-tree argmin" % ev_per_traj,
+                       "t_end": "inf", "seed": 1, "parallelism": "replicas" if ctx.world > 1 else "1 GPU",
+                       "l2": "per-channel state 16 x 44 MB, touched at random; no streaming"},
+            "events_per_step": events_all / steps, "clocks": clocks, "gpu_launches": 2 * steps,
+            "us_per_event_per_trajectory": statistics.mean(ms) * 1e3 / ev_per_traj,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "k_lazy<false>", "bytes_per_event": bytes_per_event,
+                         "touched_channels_per_event": touched, "peak_source": how,
+                         "note": "latency-bound: each event is a chain of dependent steps (slice minima, mailbox "
+                                 "exchange, fire, touched channels, group minima); the bytes moved per event are "
+                                 "~1/100 of the internal-time scan's 32 MB"}}
+
+
 # ----------------------------------------------------------------------------------------
 # Batched
 # ----------------------------------------------------------------------------------------
@@ -707,10 +783,10 @@ def main(argv=None):
     if args.workload in ("all", "ensemble"):
         line = run_ensemble(args, ctx)
         if args.workload == "all":
-            line["workloads"] = {"large": run_large(args, ctx, **sub), "batched": run_batched(args, ctx, **sub),
-                                 "grad": run_grad(args, ctx, **sub)}
+            line["workloads"] = {"large": run_large(args, ctx, **sub), "large_tree": run_large_tree(args, ctx, **sub),
+                                 "batched": run_batched(args, ctx, **sub), "grad": run_grad(args, ctx, **sub)}
     else:
-        fn = {"large": run_large, "batched": run_batched, "grad": run_grad}[args.workload]
+        fn = {"large": run_large, "large_tree": run_large_tree, "batched": run_batched, "grad": run_grad}[args.workload]
         rec = fn(args, ctx, args.steps, args.warmup)
         line = {"metric": METRIC, "value": rec.pop("value"), "unit": UNIT, "n_gpus": ctx.world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": rec.pop("ms_per_step"), "higher_is_better": True,

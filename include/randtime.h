@@ -64,7 +64,24 @@ enum {
                         N <= 4 the counts and the network too) */
   RT_MAP_WARP = 1,   /* one warp per trajectory, channels spread over lanes */
   RT_MAP_BLOCK = 2,  /* one thread block per trajectory, state in registers (M <= 8 * block_threads) */
-  RT_MAP_BUNDLE = 3  /* several blocks per trajectory, state streamed through HBM */
+  RT_MAP_BUNDLE = 3, /* several blocks per trajectory, state streamed through HBM */
+  RT_MAP_TREE = 4    /* absolute-time form only: a thread-block cluster per trajectory, min-tree
+                        argmin, only the channels an event touches updated */
+};
+
+/* Form of the method (rt_run_params.form).  Both simulate the same process with the
+ * same random numbers; in exact arithmetic they give the same path, their roundings
+ * differ, so each is bit-exact against its own definition. */
+enum {
+  RT_FORM_INTERNAL = 0, /* Table 2 in internal times: every T_k advanced at every event,
+                           T_k += a_k dt, waiting times (P_k - T_k) / a_k for all k */
+  RT_FORM_ABSOLUTE = 1  /* absolute firing times with the dependency graph (Sec. 5): channel k
+                           keeps s_k (real time of its last update) and
+                           tau_k = s_k + (P_k - T_k) / a_k; an event at t = tau_mu touches only
+                           mu and the channels reading a changed species:
+                           T_k += a_k (t - s_k), s_k = t, P_mu += E, a_k and tau_k recomputed;
+                           at the end T_k += a_k (t_f - s_k) with t_f = t_end (run reached it)
+                           or the last event time */
 };
 
 typedef struct rt_network rt_network;
@@ -89,6 +106,8 @@ typedef struct rt_run_params {
   int64_t n_traj;         /* number of trajectories, >= 0 */
   int64_t traj_offset;    /* global id of trajectory 0 (Philox counter word 1 = lo32(offset + j)) */
   double sample_dt;       /* grid spacing; <= 0: no grid.  Grid times are i*sample_dt, i < G */
+  int32_t form;           /* RT_FORM_* (0: internal-time form) */
+  int32_t reserved;
 } rt_run_params;
 
 /* Where results go.  Any pointer may be NULL (output not produced). */

@@ -18,7 +18,8 @@ i32, u32, i64, u64, dbl, vp, sz = (ctypes.c_int32, ctypes.c_uint32, ctypes.c_int
 
 RT_OK, RT_ERR_INVALID_ARG, RT_ERR_UNSUPPORTED, RT_ERR_CUDA, RT_ERR_OOM, RT_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 RT_TRAJ_TEND, RT_TRAJ_MAX_EVENTS, RT_TRAJ_ABSORBED, RT_TRAJ_OVERFLOW, RT_TRAJ_TIMEOUT, RT_TRAJ_BAD_X0 = range(6)
-RT_MAP_AUTO, RT_MAP_THREAD, RT_MAP_WARP, RT_MAP_BLOCK, RT_MAP_BUNDLE = -1, 0, 1, 2, 3
+RT_MAP_AUTO, RT_MAP_THREAD, RT_MAP_WARP, RT_MAP_BLOCK, RT_MAP_BUNDLE, RT_MAP_TREE = -1, 0, 1, 2, 3, 4
+RT_FORM_INTERNAL, RT_FORM_ABSOLUTE = 0, 1
 
 
 class rt_launch_cfg(ctypes.Structure):
@@ -27,7 +28,8 @@ class rt_launch_cfg(ctypes.Structure):
 
 class rt_run_params(ctypes.Structure):
     _fields_ = [("x0_dev", vp), ("per_traj_x0", i32), ("stream_id", u32), ("t_end", dbl), ("max_events", i64),
-                ("seed", u64), ("n_traj", i64), ("traj_offset", i64), ("sample_dt", dbl)]
+                ("seed", u64), ("n_traj", i64), ("traj_offset", i64), ("sample_dt", dbl), ("form", i32),
+                ("reserved", i32)]
 
 
 class rt_batch_policy(ctypes.Structure):

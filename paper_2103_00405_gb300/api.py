@@ -78,7 +78,7 @@ def grid_len(t_end: float, sample_dt: float) -> int:
 def simulate(net: Network, x0, t_end: float, n_traj: int, seed: int = 1, stream_id: int = 0,
              traj_offset: int = 0, max_events: int = (1 << 31) - 1, sample_dt: float = 0.0,
              grid: str = "none", grad: bool = False, mapping: Optional[int] = None, block_threads: int = 0,
-             ctas_per_traj: int = 0, trace_len: int = 0, outputs: Optional[dict] = None) -> dict:
+             ctas_per_traj: int = 0, trace_len: int = 0, form: int = 0, outputs: Optional[dict] = None) -> dict:
     """Simulate n_traj trajectories; returns a dict of CUDA tensors.
 
     x0: [N] or [n_traj, N] int32 (numpy, list or tensor; copied to the device if needed).
@@ -87,6 +87,8 @@ def simulate(net: Network, x0, t_end: float, n_traj: int, seed: int = 1, stream_
     grad: also return loglik [n_traj], counts [n_traj, M], t_internal [n_traj, M].
     trace_len: also return trace_mu [n_traj, trace_len] (fired channel of each of the first
     trace_len events, -1 after the last) and trace_t (event times, 0 after the last).
+    form: L.RT_FORM_INTERNAL (Table 2 in internal times) or L.RT_FORM_ABSOLUTE (absolute firing
+    times with the dependency graph; runs on the tree mapping).
     outputs: optional dict of preallocated tensors (same keys) to write into; missing entries are
     allocated and added to it.
     """
@@ -132,7 +134,7 @@ def simulate(net: Network, x0, t_end: float, n_traj: int, seed: int = 1, stream_
         o.trace_t_dev = _ptr(get("trace_t", (n_traj, int(trace_len)), torch.float64))
 
     p = L.rt_run_params(_ptr(x0t), per, int(stream_id), float(t_end), int(max_events), int(seed) & (2**64 - 1),
-                        int(n_traj), int(traj_offset), float(sample_dt))
+                        int(n_traj), int(traj_offset), float(sample_dt), int(form), 0)
     cfg = launch_cfg(mapping, block_threads, ctas_per_traj)
     nbytes = ctypes.c_size_t(0)
     L.check(lib.rt_workspace_bytes(net.handle, ctypes.byref(p), ctypes.byref(cfg), ctypes.byref(nbytes)),

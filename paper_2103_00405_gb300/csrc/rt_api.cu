@@ -16,8 +16,9 @@ int check_device(const rt_network *net) {
   return RT_OK;
 }
 
-static int choose_mapping(const rt_network *net, const rt_launch_cfg *cfg) {
+static int choose_mapping(const rt_network *net, const rt_launch_cfg *cfg, int form = RT_FORM_INTERNAL) {
   if (cfg && cfg->mapping != RT_MAP_AUTO) return cfg->mapping;
+  if (form == RT_FORM_ABSOLUTE) return RT_MAP_TREE;
   if (net->dev.M <= thread_mapping_max_m()) return RT_MAP_THREAD;
   if (net->dev.M <= warp_mapping_max_m()) return RT_MAP_WARP;
   if (net->dev.M <= block_mapping_max_m()) return RT_MAP_BLOCK;
@@ -40,6 +41,8 @@ int validate_run(const rt_network *net, const rt_run_params *p, const rt_outputs
   if ((o->grid_sumsq_dev || o->grid_count_dev) && !o->grid_sum_dev)
     return set_error(RT_ERR_INVALID_ARG, "grid_sumsq/grid_count need grid_sum");
   if (o->trace_len < 0) return set_error(RT_ERR_INVALID_ARG, "trace_len must be >= 0");
+  if (p->form != RT_FORM_INTERNAL && p->form != RT_FORM_ABSOLUTE)
+    return set_error(RT_ERR_INVALID_ARG, "form must be RT_FORM_INTERNAL or RT_FORM_ABSOLUTE");
   return RT_OK;
 }
 
@@ -52,10 +55,14 @@ extern "C" int rt_workspace_bytes(const rt_network *net, const rt_run_params *pa
   clear_error();
   if (!net || !params || !bytes) return set_error(RT_ERR_INVALID_ARG, "rt_workspace_bytes: NULL argument");
   *bytes = 0;
-  const int mapping = choose_mapping(net, cfg);
+  const int mapping = choose_mapping(net, cfg, params->form);
   if (mapping == RT_MAP_THREAD || mapping == RT_MAP_WARP || mapping == RT_MAP_BLOCK) return RT_OK;
   if (mapping == RT_MAP_BUNDLE) {
     *bytes = bundle_workspace_bytes(net->dev, params->n_traj, cfg ? cfg->ctas_per_traj : 0);
+    return RT_OK;
+  }
+  if (mapping == RT_MAP_TREE) {
+    *bytes = lazy_workspace_bytes(net->dev, net->max_dependents, params->n_traj, cfg ? cfg->ctas_per_traj : 0);
     return RT_OK;
   }
   return set_error(RT_ERR_UNSUPPORTED, "mapping %d not available", mapping);
@@ -81,9 +88,12 @@ extern "C" int rt_run(const rt_network *net, const rt_run_params *p, const rt_ou
   const bool want_grid = o->grid_dev || o->grid_sum_dev;
   a.G = want_grid ? rt_grid_len(p->t_end, p->sample_dt) : 0;
   a.out = *o;
-  const int mapping = choose_mapping(net, cfg);
+  const int mapping = choose_mapping(net, cfg, p->form);
   const int B = cfg ? cfg->block_threads : 0;
   cudaStream_t s = (cudaStream_t)stream;
+  if ((p->form == RT_FORM_ABSOLUTE) != (mapping == RT_MAP_TREE))
+    return set_error(RT_ERR_UNSUPPORTED, "the absolute-time form runs on the tree mapping (RT_MAP_TREE) and the "
+                     "tree mapping runs the absolute-time form only");
   switch (mapping) {
     case RT_MAP_THREAD:
       // networks of <= 4 reactions and <= 4 species: network in the parameter space, X in registers
@@ -94,6 +104,8 @@ extern "C" int rt_run(const rt_network *net, const rt_run_params *p, const rt_ou
       return launch_block_mapping(a, B, s);
     case RT_MAP_BUNDLE:
       return launch_bundle_mapping(a, cfg ? cfg->ctas_per_traj : 0, workspace, workspace_bytes, s);
+    case RT_MAP_TREE:
+      return launch_lazy_mapping(a, net->max_dependents, cfg ? cfg->ctas_per_traj : 0, workspace, workspace_bytes, s);
     default:
       return set_error(RT_ERR_UNSUPPORTED, "mapping %d not available", mapping);
   }

@@ -278,6 +278,7 @@ extern "C" int rt_batch_create(int32_t n_nets, const rt_network *const *nets, co
     d.slist = (const int32_t *)(db + g->off_slist);
     d.depmask = g->dev.depmask ? (const uint64_t *)(db + g->off_dep) : nullptr;
     d.depw = g->dev.depw ? (const uint8_t *)(db + g->off_depw) : nullptr;
+    d.vpack = g->dev.vpack ? (const int4 *)(db + g->off_vpack) : nullptr;
     hn[i].d = d;
   }
   memcpy(host.data() + off_nets, hn.data(), sizeof(BNet) * n_nets);

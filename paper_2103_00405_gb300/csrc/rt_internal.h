@@ -26,7 +26,13 @@ struct DevNet {
   const int32_t *slist;
   const uint64_t *depmask; // [M] (M <= 64 only) bit k: firing changes a species channel k reads
   const uint8_t *depw;     // [M][32] (M <= 256 only) bit r of depw[mu*32 + l]: channel l + 32 r depends on mu
+  const int4 *vpack;       // [M] net change of reaction k packed in 16 bytes (null if it does not fit):
+                           // up to 4 words (species << 8) | (delta & 0xFF), unused words 0
 };
+
+// Packed net-change word: species in the high 24 bits, delta (-128..127, never 0) in the low 8.
+__host__ __device__ inline int vpack_species(int w) { return (int)((unsigned)w >> 8); }
+__host__ __device__ inline int vpack_delta(int w) { return (int)(signed char)(w & 0xFF); }
 
 // Networks of at most kSmallM reactions and kSmallN species: the whole network by
 // value, for kernels that take it in their parameter space (rt_small.cu).
@@ -52,6 +58,7 @@ struct rt_network {
   std::string host_blob;  // the arena's bytes
   size_t off_rdesc = 0, off_c = 0, off_vptr = 0, off_vlist = 0, off_sptr = 0, off_slist = 0, off_dep = 0;
   size_t off_depw = 0;
+  size_t off_vpack = 0;
   rt::SmallNet small = {};  // filled when M <= kSmallM and N <= kSmallN
 };
 
@@ -98,5 +105,8 @@ int warp_mapping_max_m();
 int launch_block_mapping(const RunArgs &a, int block_threads, cudaStream_t s);
 int block_mapping_max_m();
 int launch_bundle_mapping(const RunArgs &a, int ctas_per_traj, void *ws, size_t ws_bytes, cudaStream_t s);
+size_t lazy_workspace_bytes(const DevNet &net, int max_dependents, int64_t n_traj, int ctas_per_traj);
+int launch_lazy_mapping(const RunArgs &a, int max_dependents, int ctas_per_traj, void *ws, size_t ws_bytes,
+                        cudaStream_t s);
 
 }  // namespace rt

@@ -179,6 +179,22 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
           depw[(size_t)k * 32 + (ch & 31)] |= (uint8_t)(1u << (ch >> 5));
         }
   }
+  // the net change of every reaction in 16 bytes, when every reaction changes at most 4
+  // species by -128..127 and N < 2^24 (one load per fired reaction in the tree mapping)
+  std::vector<int4> vpack;
+  {
+    bool fits = max_vlen <= 4 && N < (1 << 24);
+    for (size_t i = 0; i < vlist.size() && fits; i++) fits = vlist[i].y >= -128 && vlist[i].y <= 127;
+    if (fits) {
+      vpack.assign(M, make_int4(0, 0, 0, 0));
+      for (int32_t k = 0; k < M; k++) {
+        int w[4] = {0, 0, 0, 0};
+        for (int32_t i = vptr[k]; i < vptr[k + 1]; i++)
+          w[i - vptr[k]] = (int)(((unsigned)vlist[i].x << 8) | ((unsigned)vlist[i].y & 0xFFu));
+        vpack[k] = make_int4(w[0], w[1], w[2], w[3]);
+      }
+    }
+  }
   std::vector<double> cc(c, c + M);
   for (auto &x : cc)
     if (x == 0.0) x = 0.0;  // -0.0 -> +0.0 so propensities are never negative zero
@@ -194,6 +210,7 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
   g->off_slist = off; off = align_up(off + sizeof(int32_t) * std::max<size_t>(1, slist.size()), 256);
   g->off_dep = off; off = align_up(off + sizeof(uint64_t) * std::max<size_t>(1, depmask.size()), 256);
   g->off_depw = off; off = align_up(off + std::max<size_t>(1, depw.size()), 256);
+  g->off_vpack = off; off = align_up(off + sizeof(int4) * std::max<size_t>(1, vpack.size()), 256);
   g->arena_bytes = off;
   g->host_blob.assign(off, '\0');
   char *hb = &g->host_blob[0];
@@ -205,6 +222,7 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
   if (!slist.empty()) memcpy(hb + g->off_slist, slist.data(), sizeof(int32_t) * slist.size());
   if (!depmask.empty()) memcpy(hb + g->off_dep, depmask.data(), sizeof(uint64_t) * depmask.size());
   if (!depw.empty()) memcpy(hb + g->off_depw, depw.data(), depw.size());
+  if (!vpack.empty()) memcpy(hb + g->off_vpack, vpack.data(), sizeof(int4) * vpack.size());
 
   cudaGetDevice(&g->device);
   cudaError_t e = cudaMalloc(&g->arena, g->arena_bytes);
@@ -233,6 +251,7 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
   d.slist = (const int32_t *)(db + g->off_slist);
   d.depmask = M <= 64 ? (const uint64_t *)(db + g->off_dep) : nullptr;
   d.depw = M <= 256 ? (const uint8_t *)(db + g->off_depw) : nullptr;
+  d.vpack = vpack.empty() ? nullptr : (const int4 *)(db + g->off_vpack);
   g->max_dependents = max_dep;
   g->n_dep_nz = dep_nz;
   if (M <= kSmallM && N <= kSmallN) {
