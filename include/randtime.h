@@ -62,7 +62,7 @@ enum {
   RT_MAP_AUTO = -1,  /* chosen by the library from the network size */
   RT_MAP_THREAD = 0, /* one thread per trajectory, state in registers (M <= 16; with M <= 4 and
                         N <= 4 the counts and the network too) */
-  RT_MAP_WARP = 1,   /* one warp per trajectory, channels spread over lanes */
+  RT_MAP_WARP = 1,   /* a warp segment (8, 16 or 32 lanes) per trajectory, channels spread over lanes */
   RT_MAP_BLOCK = 2,  /* one thread block per trajectory, state in registers (M <= 8 * block_threads) */
   RT_MAP_BUNDLE = 3, /* several blocks per trajectory, state streamed through HBM */
   RT_MAP_TREE = 4    /* absolute-time form only: a thread-block cluster per trajectory, min-tree
@@ -91,8 +91,9 @@ typedef struct rt_batch rt_batch;
 typedef struct rt_launch_cfg {
   int32_t mapping;       /* RT_MAP_* */
   int32_t block_threads; /* threads per block */
-  int32_t ctas_per_traj; /* RT_MAP_BUNDLE: blocks cooperating on one trajectory */
-  int32_t reserved;
+  int32_t ctas_per_traj; /* RT_MAP_BUNDLE, RT_MAP_TREE: blocks cooperating on one trajectory */
+  int32_t lanes_per_traj; /* RT_MAP_WARP: lanes per trajectory (8, 16 or 32; 32 / lanes
+                             trajectories share a warp, at most 8 channels per lane) */
 } rt_launch_cfg;
 
 /* What to simulate. */

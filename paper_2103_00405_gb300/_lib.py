@@ -23,7 +23,7 @@ RT_FORM_INTERNAL, RT_FORM_ABSOLUTE = 0, 1
 
 
 class rt_launch_cfg(ctypes.Structure):
-    _fields_ = [("mapping", i32), ("block_threads", i32), ("ctas_per_traj", i32), ("reserved", i32)]
+    _fields_ = [("mapping", i32), ("block_threads", i32), ("ctas_per_traj", i32), ("lanes_per_traj", i32)]
 
 
 class rt_run_params(ctypes.Structure):

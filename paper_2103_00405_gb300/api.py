@@ -66,9 +66,10 @@ class Network:
             pass
 
 
-def launch_cfg(mapping: Optional[int] = None, block_threads: int = 0, ctas_per_traj: int = 0):
+def launch_cfg(mapping: Optional[int] = None, block_threads: int = 0, ctas_per_traj: int = 0,
+               lanes_per_traj: int = 0):
     return L.rt_launch_cfg(L.RT_MAP_AUTO if mapping is None else int(mapping), int(block_threads),
-                           int(ctas_per_traj), 0)
+                           int(ctas_per_traj), int(lanes_per_traj))
 
 
 def grid_len(t_end: float, sample_dt: float) -> int:
@@ -78,7 +79,8 @@ def grid_len(t_end: float, sample_dt: float) -> int:
 def simulate(net: Network, x0, t_end: float, n_traj: int, seed: int = 1, stream_id: int = 0,
              traj_offset: int = 0, max_events: int = (1 << 31) - 1, sample_dt: float = 0.0,
              grid: str = "none", grad: bool = False, mapping: Optional[int] = None, block_threads: int = 0,
-             ctas_per_traj: int = 0, trace_len: int = 0, form: int = 0, outputs: Optional[dict] = None) -> dict:
+             ctas_per_traj: int = 0, trace_len: int = 0, form: int = 0, lanes_per_traj: int = 0,
+             outputs: Optional[dict] = None) -> dict:
     """Simulate n_traj trajectories; returns a dict of CUDA tensors.
 
     x0: [N] or [n_traj, N] int32 (numpy, list or tensor; copied to the device if needed).
@@ -135,7 +137,7 @@ def simulate(net: Network, x0, t_end: float, n_traj: int, seed: int = 1, stream_
 
     p = L.rt_run_params(_ptr(x0t), per, int(stream_id), float(t_end), int(max_events), int(seed) & (2**64 - 1),
                         int(n_traj), int(traj_offset), float(sample_dt), int(form), 0)
-    cfg = launch_cfg(mapping, block_threads, ctas_per_traj)
+    cfg = launch_cfg(mapping, block_threads, ctas_per_traj, lanes_per_traj)
     nbytes = ctypes.c_size_t(0)
     L.check(lib.rt_workspace_bytes(net.handle, ctypes.byref(p), ctypes.byref(cfg), ctypes.byref(nbytes)),
             "rt_workspace_bytes")

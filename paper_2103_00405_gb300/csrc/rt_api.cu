@@ -99,7 +99,7 @@ extern "C" int rt_run(const rt_network *net, const rt_run_params *p, const rt_ou
       // networks of <= 4 reactions and <= 4 species: network in the parameter space, X in registers
       return net->small.ok ? launch_small_mapping(a, net->small, B, s) : launch_thread_mapping(a, B, s);
     case RT_MAP_WARP:
-      return launch_warp_mapping(a, B, s);
+      return launch_warp_mapping(a, B, cfg ? cfg->lanes_per_traj : 0, s);
     case RT_MAP_BLOCK:
       return launch_block_mapping(a, B, s);
     case RT_MAP_BUNDLE:

@@ -129,10 +129,10 @@ __global__ void __launch_bounds__(512, 2) k_batch(const BatchArgs B) {
         int *X = (int *)smem + warp * B.maxN_warp;
         const int tf = isfinite(A.t_end) ? 1 : 0;
         switch (bn.R) {
-          case 1: warp_trajectory<1, LL>(A, net, X, nullptr, j, tf); break;
-          case 2: warp_trajectory<2, LL>(A, net, X, nullptr, j, tf); break;
-          case 4: warp_trajectory<4, LL>(A, net, X, nullptr, j, tf); break;
-          default: warp_trajectory<8, LL>(A, net, X, nullptr, j, tf); break;
+          case 1: warp_trajectories<1, 32, LL>(A, net, X, nullptr, j, tf); break;
+          case 2: warp_trajectories<2, 32, LL>(A, net, X, nullptr, j, tf); break;
+          case 4: warp_trajectories<4, 32, LL>(A, net, X, nullptr, j, tf); break;
+          default: warp_trajectories<8, 32, LL>(A, net, X, nullptr, j, tf); break;
         }
       }
       continue;
@@ -278,6 +278,8 @@ extern "C" int rt_batch_create(int32_t n_nets, const rt_network *const *nets, co
     d.slist = (const int32_t *)(db + g->off_slist);
     d.depmask = g->dev.depmask ? (const uint64_t *)(db + g->off_dep) : nullptr;
     d.depw = g->dev.depw ? (const uint8_t *)(db + g->off_depw) : nullptr;
+    d.depw16 = g->dev.depw16 ? (const uint8_t *)(db + g->off_depw16) : nullptr;
+    d.depw8 = g->dev.depw8 ? (const uint8_t *)(db + g->off_depw8) : nullptr;
     d.vpack = g->dev.vpack ? (const int4 *)(db + g->off_vpack) : nullptr;
     hn[i].d = d;
   }

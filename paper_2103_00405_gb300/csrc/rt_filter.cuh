@@ -34,6 +34,24 @@ __device__ __forceinline__ float f32_upper(double x) {
   return hi >= (1151u << 20) ? __int_as_float(0x7F800000) : __uint_as_float(f);
 }
 
+// A float upper bound of the waiting time w = fl(fl(P - T) / a) of Eq. 25 (a > 0, T >= 0):
+// an upper bound of P - T over a lower bound of a, divided with __fdividef (documented: at
+// most 2 ulp from the rounded quotient for divisors in [2^-126, 2^126]) and widened by
+// 2^-18, which also covers the two binary64 roundings; +inf for divisors outside that range.
+// 0 when P - T is certainly <= 0 (then w = 0).
+__device__ __forceinline__ float quot_upper(double P, double T, double a) {
+  const float rem = __fsub_ru(f32_upper(P), f32_lower(T));
+  if (!(rem > 0.0f)) return 0.0f;
+  const float alo = f32_lower(a);
+  if (!(alo >= 0x1p-125f) || alo > 0x1p125f) return __int_as_float(0x7F800000);
+  return __fmul_ru(__fdividef(rem, alo), 1.000003814697265625f);  // 1 + 2^-18
+}
+
+// The next float above a finite x >= 0 (+inf stays +inf).
+__device__ __forceinline__ float f32_next_up(float x) {
+  return x < __int_as_float(0x7F800000) ? __int_as_float(__float_as_int(x) + 1) : x;
+}
+
 // True if the exact (P - T) / a is certainly > thr (a > 0, T >= 0, thr >= 0).
 __device__ __forceinline__ bool exceeds(double P, double T, double a, float thr) {
   const float rem_lo = __fsub_rd(f32_lower(P), f32_upper(T));

@@ -168,17 +168,22 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
       for (int32_t i = vptr[k]; i < vptr[k + 1]; i++)
         for (int32_t q = sptr[vlist[i].x]; q < sptr[vlist[i].x + 1]; q++) depmask[k] |= 1ull << slist[q];
   }
-  // per reaction and lane: which of the lane's channels (l + 32 r) read a changed species
-  std::vector<uint8_t> depw;
-  if (M <= 256) {
-    depw.assign((size_t)M * 32, 0);
+  // per reaction and lane of a G-lane segment: which of the lane's channels (l + G r, r < 8)
+  // read a changed species
+  auto dep_bytes = [&](int G) {
+    std::vector<uint8_t> d((size_t)M * G, 0);
     for (int32_t k = 0; k < M; k++)
       for (int32_t i = vptr[k]; i < vptr[k + 1]; i++)
         for (int32_t q = sptr[vlist[i].x]; q < sptr[vlist[i].x + 1]; q++) {
           const int32_t ch = slist[q];
-          depw[(size_t)k * 32 + (ch & 31)] |= (uint8_t)(1u << (ch >> 5));
+          d[(size_t)k * G + (ch % G)] |= (uint8_t)(1u << (ch / G));
         }
-  }
+    return d;
+  };
+  std::vector<uint8_t> depw, depw16, depw8;
+  if (M <= 256) depw = dep_bytes(32);
+  if (M <= 128) depw16 = dep_bytes(16);
+  if (M <= 64) depw8 = dep_bytes(8);
   // the net change of every reaction in 16 bytes, when every reaction changes at most 4
   // species by -128..127 and N < 2^24 (one load per fired reaction in the tree mapping)
   std::vector<int4> vpack;
@@ -210,6 +215,8 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
   g->off_slist = off; off = align_up(off + sizeof(int32_t) * std::max<size_t>(1, slist.size()), 256);
   g->off_dep = off; off = align_up(off + sizeof(uint64_t) * std::max<size_t>(1, depmask.size()), 256);
   g->off_depw = off; off = align_up(off + std::max<size_t>(1, depw.size()), 256);
+  g->off_depw16 = off; off = align_up(off + std::max<size_t>(1, depw16.size()), 256);
+  g->off_depw8 = off; off = align_up(off + std::max<size_t>(1, depw8.size()), 256);
   g->off_vpack = off; off = align_up(off + sizeof(int4) * std::max<size_t>(1, vpack.size()), 256);
   g->arena_bytes = off;
   g->host_blob.assign(off, '\0');
@@ -222,6 +229,8 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
   if (!slist.empty()) memcpy(hb + g->off_slist, slist.data(), sizeof(int32_t) * slist.size());
   if (!depmask.empty()) memcpy(hb + g->off_dep, depmask.data(), sizeof(uint64_t) * depmask.size());
   if (!depw.empty()) memcpy(hb + g->off_depw, depw.data(), depw.size());
+  if (!depw16.empty()) memcpy(hb + g->off_depw16, depw16.data(), depw16.size());
+  if (!depw8.empty()) memcpy(hb + g->off_depw8, depw8.data(), depw8.size());
   if (!vpack.empty()) memcpy(hb + g->off_vpack, vpack.data(), sizeof(int4) * vpack.size());
 
   cudaGetDevice(&g->device);
@@ -251,6 +260,8 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
   d.slist = (const int32_t *)(db + g->off_slist);
   d.depmask = M <= 64 ? (const uint64_t *)(db + g->off_dep) : nullptr;
   d.depw = M <= 256 ? (const uint8_t *)(db + g->off_depw) : nullptr;
+  d.depw16 = M <= 128 ? (const uint8_t *)(db + g->off_depw16) : nullptr;
+  d.depw8 = M <= 64 ? (const uint8_t *)(db + g->off_depw8) : nullptr;
   d.vpack = vpack.empty() ? nullptr : (const int4 *)(db + g->off_vpack);
   g->max_dependents = max_dep;
   g->n_dep_nz = dep_nz;

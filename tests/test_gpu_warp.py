@@ -1,5 +1,6 @@
-"""Warp-per-trajectory mapping (networks of 17..256 reactions) against the CPU oracle,
-bit for bit, including the gradient workload (M = 64, N = 16) and its backward kernel."""
+"""Warp-segment mapping (8, 16 or 32 lanes per trajectory; networks of 17..256 reactions)
+against the CPU oracle, bit for bit, including the gradient workload (M = 64, N = 16) and its
+backward kernel."""
 import numpy as np
 import pytest
 
@@ -33,6 +34,42 @@ def test_warp_mapping_bit_exact(M, N):
     o = oracle.run(net, x0, 0.5, 45, seed=M, stream_id=2, traj_offset=5, max_events=30000, sample_dt=0.05,
                    want_grid=True, want_grad=True, n_threads=16)
     assert_same(g, o)
+
+
+@pytest.mark.parametrize("G,M,N", [(8, 17, 5), (8, 29, 7), (8, 64, 16), (16, 40, 9), (16, 100, 25), (16, 128, 30),
+                                   (32, 17, 5), (32, 64, 16), (32, 200, 50)])
+@pytest.mark.parametrize("n_traj", [1, 7, 45])
+def test_warp_segments_bit_exact_for_every_width(G, M, N, n_traj):
+    """Several trajectories per warp advance together (4 with 8 lanes each, 2 with 16); trajectory
+    counts that leave a warp partly empty, ragged channel counts, likelihood, grid and trace."""
+    net = W.random_mass_action(N, M, seed=700 + M, c_sigma=0.7)
+    rng = np.random.default_rng(M + n_traj)
+    x0 = rng.integers(0, 30, size=(n_traj, N)).astype(np.int32)
+    if n_traj > 3:
+        x0[3, 0] = -1  # one trajectory in a shared warp starts from a bad state
+    netg = api.Network(net)
+    g = api.simulate(netg, x0, 0.4, n_traj, seed=M, stream_id=1, traj_offset=9, max_events=20000, sample_dt=0.05,
+                     grid="traj", grad=True, mapping=L.RT_MAP_WARP, lanes_per_traj=G, trace_len=300)
+    o = oracle.run(net, x0, 0.4, n_traj, seed=M, stream_id=1, traj_offset=9, max_events=20000, sample_dt=0.05,
+                   want_grid=True, want_grad=True, trace_len=300, n_threads=16)
+    assert_same(g, o)
+    for k in ("trace_mu", "trace_t"):
+        a, b = g[k].cpu().numpy(), o[k]
+        assert np.array_equal(a.view(np.int64) if a.dtype == np.float64 else a,
+                              b.view(np.int64) if b.dtype == np.float64 else b), k
+
+
+def test_warp_segments_with_uneven_event_counts_and_caps():
+    """Trajectories sharing a warp finish at different events (caps, absorption, t_end); the
+    others keep going with the finished lanes idle."""
+    death = W._from_lists(2, [({0: 1}, {}, 1.0), ({1: 1}, {}, 2.0)] * 12, "death24")
+    x0 = np.array([[3, 4], [0, 0], [40, 1], [7, 7], [1, 300], [2, 2], [9, 0]], np.int32)
+    for G in (8, 16, 32):
+        for cap in (5, 10**6):
+            g = api.simulate(api.Network(death), x0, 3.0, 7, seed=2, grad=True, max_events=cap,
+                             mapping=L.RT_MAP_WARP, lanes_per_traj=G)
+            o = oracle.run(death, x0, 3.0, 7, seed=2, want_grad=True, max_events=cap)
+            assert_same(g, o)
 
 
 def test_warp_mapping_is_the_default_for_mid_size_networks():
