@@ -163,6 +163,17 @@ void rt_network_destroy(rt_network *net);
 int rt_network_info(const rt_network *net, int32_t *n_species, int32_t *n_reactions,
                     int32_t *max_dependents, int64_t *n_dependency_nz);
 
+/*
+ * rt_network_set_enabled -- forbid channels to fire (the paper's boundary conditions:
+ * a forbidden channel is given a frozen internal time, Table 2's note).  enabled: host
+ * array [n_reactions], 0 = forbidden (its propensity is taken as 0, so its internal
+ * time stays frozen and it never fires); NULL enables every channel.  The network's
+ * own rates are kept: rt_loglik_backward still divides by them, so a forbidden
+ * channel's gradient is 0.  Copies to the device synchronously; no work using the
+ * network may be in flight.  Batches created afterwards take the setting with them.
+ */
+int rt_network_set_enabled(rt_network *net, const uint8_t *enabled);
+
 /* Number of grid points on [0, t_end] for spacing sample_dt:
  * floor(t_end / sample_dt * (1 + 1e-12)) + 1, or 0 if sample_dt <= 0 or t_end is not finite. */
 int64_t rt_grid_len(double t_end, double sample_dt);
@@ -335,6 +346,38 @@ int rt_batch_run(rt_batch *batch, const int32_t *x0_dev, const double *t_end_dev
  * happens (it keeps the loop from being optimised away).
  */
 int rt_fp64_probe(int64_t iters, int32_t blocks_per_sm, double *sink_dev, double *ops, void *stream);
+
+/*
+ * Model files (the text format of the paper's Table 4, Sec. 5):
+ *   // comment
+ *   # init
+ *   A = 1000                      initial counts
+ *   # reactions
+ *   1 A 1 B --> 2 B : 0.01        coef name ... --> coef name ... : rate (NULL: none;
+ *                                 a coefficient 1 may be omitted; "->" also accepted)
+ *   # end
+ *   time = 2                      settings after "# end"
+ *   steps = 10000
+ * Species are numbered in order of first appearance; species that appear only in
+ * reactions start at 0.  The network comes out in the COO form of rt_network_create.
+ */
+typedef struct rt_model {
+  int32_t n_species, n_reactions;
+  int64_t n_reac_nz;
+  int32_t *reac_rxn, *reac_sp, *reac_coef;  /* reactant coefficients (merged per species) */
+  int64_t n_stoi_nz;
+  int32_t *stoi_rxn, *stoi_sp, *stoi_delta; /* net state changes (nonzero only) */
+  double *c;                                /* [n_reactions] rates */
+  int32_t *x0;                              /* [n_species] initial counts */
+  char **species_names;                     /* [n_species] NUL-terminated names */
+  double time;                              /* "time" setting, NaN if absent */
+  int64_t steps;                            /* "steps" setting, -1 if absent */
+} rt_model;
+
+/* Parse model text (host, NUL-terminated).  On success *out is owned by the library until
+ * rt_model_free.  Malformed text returns RT_ERR_INVALID_ARG with the line in rt_last_error. */
+int rt_model_parse(const char *text, rt_model **out);
+void rt_model_free(rt_model *model);
 
 /* Message describing the last error on this host thread ("" if none). */
 const char *rt_last_error(void);

@@ -107,7 +107,7 @@ def grid_len(t_end: float, sample_dt: float, lib=None) -> int:
     return int((lib or load()).oracle_grid_len(float(t_end), float(sample_dt)))
 
 
-MODE_EAGER, MODE_LAZY = 0, 1
+MODE_EAGER, MODE_LAZY, MODE_RESCALED = 0, 1, 2
 
 
 def run(net, x0, t_end, n_traj, seed=1, stream_id=0, traj_offset=0, max_events=(1 << 31) - 1,
@@ -116,7 +116,8 @@ def run(net, x0, t_end, n_traj, seed=1, stream_id=0, traj_offset=0, max_events=(
     """Run the oracle; returns a dict of numpy arrays.
 
     x0 is [N] (shared) or [n_traj, N] (per trajectory).  mode: MODE_EAGER (Table 2 in
-    internal-time form) or MODE_LAZY (absolute-time form with the dependency graph).
+    internal-time form), MODE_LAZY (absolute-time form with the dependency graph) or
+    MODE_RESCALED (Table 3's rescaled waiting times, every propensity recomputed).
     enabled: optional [M] flags; channels with 0 never fire (frozen internal time).
     """
     lib = lib or load()

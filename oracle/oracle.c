@@ -46,6 +46,15 @@
  *      internal time is first brought up to the event, T_k += a_k (t - s_k), then
  *      a_k and tau_k are recomputed); every other tau_k stays as it is.  In exact
  *      arithmetic both modes give the same path; their roundings differ.
+ *   2  Table 3's form ("parallel NRRTA"): each channel keeps its relative waiting
+ *      time w_k and the propensity p_k it was computed with; after an event that
+ *      took dt, every propensity is recomputed (no dependency graph) and every
+ *      other channel's waiting time is rescaled, w_k = (p_k / a_k) (w_k - dt); the
+ *      fired channel draws w_mu = E / a_mu; then p_k = a_k (the update Table 3
+ *      leaves implicit).  A channel whose propensity drops to 0 keeps its remaining
+ *      internal time q_k = p_k (w_k - dt) frozen (w_k = +inf) and resumes with
+ *      w_k = q_k / a_k.  Internal times for the likelihood accumulate T_k += a_k dt.
+ *      Same path as modes 0 and 1 in exact arithmetic.
  * enabled (NULL = all): a channel with enabled[k] == 0 is forbidden to fire; its
  * propensity is taken as 0, so its internal time is frozen (Table 2's note on
  * boundary conditions).
@@ -576,6 +585,114 @@ static void run_traj_lazy(const job_t *J, int64_t j, double *P, double *T, doubl
   if (J->t_last) J->t_last[j] = t;
 }
 
+/* Mode 2: Table 3's rescaled form (see the header).  w: relative waiting times, p: the
+ * propensities they were computed with, q: frozen remaining internal times. */
+static void run_traj_rescaled(const job_t *J, int64_t j, double *w, double *T, double *a, int32_t *n, int32_t *X,
+                              double *p, double *q) {
+  const onet *g = J->g;
+  const int32_t N = g->N, M = g->M;
+  const uint64_t gid = (uint64_t)(J->traj_offset + j);
+  const int32_t *x0 = J->x0 + (J->per_traj_x0 ? j * (int64_t)N : 0);
+  int32_t *grid = J->grid ? J->grid + j * J->G * N : NULL;
+  int32_t *trace_mu = J->trace_mu ? J->trace_mu + j * J->trace_len : NULL;
+  double *trace_t = J->trace_t ? J->trace_t + j * J->trace_len : NULL;
+  for (int64_t i = 0; i < J->trace_len; i++) {
+    if (trace_mu) trace_mu[i] = -1;
+    if (trace_t) trace_t[i] = 0.0;
+  }
+  int32_t status = ST_TEND;
+  int bad = 0;
+  for (int32_t i = 0; i < N; i++) {
+    X[i] = x0[i];
+    if (x0[i] < 0) bad = 1;
+  }
+  double t = 0.0, ll = 0.0;
+  int64_t ev = 0, gi = 0;
+  for (int32_t k = 0; k < M; k++) { n[k] = 0; T[k] = 0.0; a[k] = 0.0; }
+
+  if (bad) {
+    status = ST_BAD_X0;
+  } else {
+    /* initialise (Table 3): a_k, dt_k = ln(1/r_k) / a_k, p_k = a_k */
+    for (int32_t k = 0; k < M; k++) {
+      double E = oracle_exp1(J->seed, gid, (uint32_t)k, 0, J->stream);
+      a[k] = propensity(g, k, X);
+      p[k] = a[k];
+      if (a[k] > 0.0) { w[k] = E / a[k]; q[k] = 0.0; }
+      else { w[k] = INFINITY; q[k] = E; }
+    }
+    for (;;) {
+      /* scan for the smallest waiting time; ties go to the smallest index */
+      double dmin = INFINITY;
+      int32_t mu = -1;
+      for (int32_t k = 0; k < M; k++)
+        if (w[k] < dmin) { dmin = w[k]; mu = k; }
+      if (mu < 0) { status = ST_ABSORBED; break; }
+      double tn = t + dmin;
+      if (tn > J->t_end) { status = ST_TEND; break; }
+      if (ev == J->max_events) { status = ST_MAX_EVENTS; break; }
+      int over = 0;
+      for (int64_t i = g->vptr[mu]; i < g->vptr[mu + 1]; i++) {
+        int64_t nx = (int64_t)X[g->vsp[i]] + g->vdel[i];
+        if (nx > INT32_MAX || nx < 0) over = 1;
+      }
+      if (over) { status = ST_OVERFLOW; break; }
+      if (grid)
+        while (gi < J->G && (double)gi * J->sample_dt < tn) {
+          memcpy(grid + gi * N, X, sizeof(int32_t) * (size_t)N);
+          gi++;
+        }
+      else
+        while (gi < J->G && (double)gi * J->sample_dt < tn) gi++;
+      t = tn;
+      for (int32_t k = 0; k < M; k++) T[k] = T[k] + a[k] * dmin;
+      if (J->loglik) ll = ll + oracle_rt_log(a[mu]);
+      for (int64_t i = g->vptr[mu]; i < g->vptr[mu + 1]; i++) X[g->vsp[i]] += g->vdel[i];
+      if (trace_mu && ev < J->trace_len) { trace_mu[ev] = mu; trace_t[ev] = t; }
+      n[mu] += 1;
+      ev += 1;
+      /* recalculate every propensity; rescale every other waiting time; redraw the fired one */
+      for (int32_t k = 0; k < M; k++) {
+        double an = propensity(g, k, X);
+        if (k == mu) {
+          double E = oracle_exp1(J->seed, gid, (uint32_t)mu,
+                                 (uint64_t)(ORACLE_MUTANT == 20 ? n[mu] - 1 : n[mu]), J->stream);
+          if (an > 0.0) w[k] = E / an;
+          else { q[k] = E; w[k] = INFINITY; }
+        } else if (p[k] > 0.0) {
+          double rem = w[k] - dmin;
+          if (an > 0.0) w[k] = ORACLE_MUTANT == 19 ? rem : (p[k] / an) * rem;
+          else { q[k] = p[k] * rem; w[k] = INFINITY; }
+        } else if (an > 0.0) {
+          w[k] = (ORACLE_MUTANT == 21 ? 0.0 : q[k]) / an;
+        }
+        p[k] = an;
+        a[k] = an;
+      }
+    }
+  }
+
+  if (grid)
+    for (; gi < J->G; gi++)
+      for (int32_t i = 0; i < N; i++)
+        grid[gi * N + i] = (status == ST_TEND || status == ST_ABSORBED) ? X[i] : -1;
+  if (status != ST_BAD_X0 && (status == ST_TEND || status == ST_ABSORBED) && isfinite(J->t_end)) {
+    double rest = J->t_end - t;
+    for (int32_t k = 0; k < M; k++) T[k] = T[k] + a[k] * rest;
+  }
+  if (J->loglik) {
+    double sT = 0.0;
+    for (int32_t k = 0; k < M; k++) sT = sT + T[k];
+    J->loglik[j] = status == ST_BAD_X0 ? NAN : ll - sT;
+  }
+  if (J->counts) memcpy(J->counts + j * (int64_t)M, n, sizeof(int32_t) * (size_t)M);
+  if (J->t_internal) memcpy(J->t_internal + j * (int64_t)M, T, sizeof(double) * (size_t)M);
+  if (J->x_final) memcpy(J->x_final + j * (int64_t)N, X, sizeof(int32_t) * (size_t)N);
+  if (J->n_events) J->n_events[j] = ev;
+  if (J->status) J->status[j] = status;
+  if (J->t_last) J->t_last[j] = t;
+}
+
 static void *worker(void *arg) {
   job_t *J = (job_t *)arg;
   int32_t M = J->g->M, N = J->g->N;
@@ -589,6 +706,7 @@ static void *worker(void *arg) {
   } else {
     for (int64_t j = J->j0; j < J->j1; j++) {
       if (J->mode == 1) run_traj_lazy(J, j, P, T, a, n, X, s, tau, upd, chg);
+      else if (J->mode == 2) run_traj_rescaled(J, j, P, T, a, n, X, s, tau);
       else run_traj(J, j, P, T, a, n, X);
     }
   }
@@ -598,7 +716,8 @@ static void *worker(void *arg) {
 
 /*
  * Run n_traj trajectories (global ids traj_offset + j) of one network in the given
- * mode (0: Table 2 internal-time form, 1: absolute-time form; see the header).
+ * mode (0: Table 2 internal-time form, 1: absolute-time form, 2: Table 3's rescaled
+ * form; see the header).
  * Output arrays may be NULL.  Returns 0, -1 for invalid arguments, -4 for
  * allocation failure.
  */
@@ -611,7 +730,7 @@ int oracle_run(int32_t mode, int32_t N, int32_t M,
                int32_t *x_final, int32_t *grid, int64_t *n_events, int32_t *status, double *t_last,
                double *loglik, int32_t *counts, double *t_internal,
                int64_t trace_len, int32_t *trace_mu, double *trace_t, int32_t n_threads) {
-  if (mode < 0 || mode > 1 || N < 1 || M < 1 || n_traj < 0 || max_events < 0 || t_end != t_end) return -1;
+  if (mode < 0 || mode > 2 || N < 1 || M < 1 || n_traj < 0 || max_events < 0 || t_end != t_end) return -1;
   for (int64_t i = 0; i < n_reac_nz; i++)
     if (reac_rxn[i] < 0 || reac_rxn[i] >= M || reac_sp[i] < 0 || reac_sp[i] >= N || reac_coef[i] <= 0)
       return -1;

@@ -49,11 +49,22 @@ class rt_batch_outputs(ctypes.Structure):
                 ("trace_mu_dev", vp), ("trace_t_dev", vp)]
 
 
+class rt_model(ctypes.Structure):
+    _fields_ = [("n_species", i32), ("n_reactions", i32), ("n_reac_nz", i64), ("reac_rxn", ctypes.POINTER(i32)),
+                ("reac_sp", ctypes.POINTER(i32)), ("reac_coef", ctypes.POINTER(i32)), ("n_stoi_nz", i64),
+                ("stoi_rxn", ctypes.POINTER(i32)), ("stoi_sp", ctypes.POINTER(i32)), ("stoi_delta", ctypes.POINTER(i32)),
+                ("c", ctypes.POINTER(dbl)), ("x0", ctypes.POINTER(i32)), ("species_names", ctypes.POINTER(ctypes.c_char_p)),
+                ("time", dbl), ("steps", i64)]
+
+
 # (name, restype, argtypes) of every entry point declared in include/randtime.h
 SIGNATURES = [
     ("rt_network_create", ctypes.c_int, [i32, i32, i64, vp, vp, vp, i64, vp, vp, vp, vp, ctypes.POINTER(vp)]),
     ("rt_network_destroy", None, [vp]),
     ("rt_network_info", ctypes.c_int, [vp, vp, vp, vp, vp]),
+    ("rt_network_set_enabled", ctypes.c_int, [vp, vp]),
+    ("rt_model_parse", ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.POINTER(rt_model))]),
+    ("rt_model_free", None, [ctypes.POINTER(rt_model)]),
     ("rt_grid_len", i64, [dbl, dbl]),
     ("rt_workspace_bytes", ctypes.c_int, [vp, ctypes.POINTER(rt_run_params), ctypes.POINTER(rt_launch_cfg),
                                           ctypes.POINTER(sz)]),

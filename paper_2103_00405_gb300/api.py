@@ -47,6 +47,16 @@ class Network:
         self.N, self.M = s.n_species, s.n_reactions
         self.device = torch.cuda.current_device()
 
+    def set_enabled(self, enabled=None):
+        """Forbid channels to fire (enabled[k] == 0): their internal times stay frozen (Table 2's
+        note on boundary conditions).  None enables every channel."""
+        en = None if enabled is None else np.ascontiguousarray(enabled, dtype=np.uint8)
+        if en is not None and en.shape != (self.M,):
+            raise ValueError("enabled must have one entry per reaction")
+        L.check(self.lib.rt_network_set_enabled(self.handle, None if en is None else en.ctypes.data_as(ctypes.c_void_p)),
+                "rt_network_set_enabled")
+        return self
+
     def info(self):
         n, m, md = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         nz = ctypes.c_int64()
@@ -194,9 +204,13 @@ class Batch:
     """
 
     def __init__(self, specs, thread_max_m: int = 8, warp_max_m: int = 256, block_threads: int = 512,
-                 blocks_per_sm: int = 0, stream_ids=None):
+                 blocks_per_sm: int = 0, stream_ids=None, enabled=None):
         self.lib = L.load()
         nets = [Network(s) for s in specs]
+        if enabled is not None:  # per network: forbidden channels (Network.set_enabled), or None
+            for n, e in zip(nets, enabled):
+                if e is not None:
+                    n.set_enabled(e)
         arr = (ctypes.c_void_p * len(nets))(*[n.handle.value for n in nets])
         pol = L.rt_batch_policy(thread_max_m, warp_max_m, block_threads, blocks_per_sm)
         h = ctypes.c_void_p()
@@ -353,3 +367,27 @@ def fp64_probe(iters: int = 4096, blocks_per_sm: int = 8, repeats: int = 3):
         b.synchronize()
         best = max(best, ops.value / (a.elapsed_time(b) / 1e3))
     return best
+
+
+def parse_model(text: str):
+    """Parse a model in the text format of the paper's Table 4 (rt_model_parse).  Returns a dict:
+    net (a workloads.Network), x0 (int32 [N]), names, time (None if absent), steps (None if absent)."""
+    lib = L.load()
+    p = ctypes.POINTER(L.rt_model)()
+    L.check(lib.rt_model_parse(text.encode(), ctypes.byref(p)), "rt_model_parse")
+    try:
+        m = p.contents
+        N, M = m.n_species, m.n_reactions
+
+        def arr(ptr, n, dt):
+            return np.ctypeslib.as_array(ptr, shape=(n,)).astype(dt).copy() if n else np.zeros(0, dt)
+
+        net = NetworkSpec(N, M, arr(m.reac_rxn, m.n_reac_nz, np.int32), arr(m.reac_sp, m.n_reac_nz, np.int32),
+                          arr(m.reac_coef, m.n_reac_nz, np.int32), arr(m.stoi_rxn, m.n_stoi_nz, np.int32),
+                          arr(m.stoi_sp, m.n_stoi_nz, np.int32), arr(m.stoi_delta, m.n_stoi_nz, np.int32),
+                          arr(m.c, M, np.float64), "model")
+        names = [m.species_names[i].decode() for i in range(N)]
+        return dict(net=net, x0=arr(m.x0, N, np.int32), names=names,
+                    time=None if math.isnan(m.time) else float(m.time), steps=None if m.steps < 0 else int(m.steps))
+    finally:
+        lib.rt_model_free(p)

@@ -214,7 +214,7 @@ extern "C" int rt_loglik_backward(const rt_network *net, int64_t n_traj, const d
   if (rc) return rc;
   const int M = net->dev.M;
   dim3 block(32, 32);
-  k_loglik_backward<<<(M + 31) / 32, block, 0, (cudaStream_t)stream>>>(M, n_traj, grad_ll, counts, Tend, net->dev.c,
+  k_loglik_backward<<<(M + 31) / 32, block, 0, (cudaStream_t)stream>>>(M, n_traj, grad_ll, counts, Tend, net->dev.c0,
                                                                      grad_c);
   const cudaError_t err = cudaGetLastError();
   return err == cudaSuccess ? RT_OK : set_error(RT_ERR_CUDA, "%s", cudaGetErrorString(err));

@@ -272,6 +272,7 @@ extern "C" int rt_batch_create(int32_t n_nets, const rt_network *const *nets, co
     DevNet d = g->dev;  // same layout, rebased into the batch arena
     d.rdesc = (const int2 *)(db + g->off_rdesc);
     d.c = (const double *)(db + g->off_c);
+    d.c0 = (const double *)(db + g->off_c0);
     d.vptr = (const int32_t *)(db + g->off_vptr);
     d.vlist = (const int2 *)(db + g->off_vlist);
     d.sptr = (const int32_t *)(db + g->off_sptr);

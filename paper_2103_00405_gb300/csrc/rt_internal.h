@@ -3,6 +3,9 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
 
 #include "randtime.h"
 
@@ -19,7 +22,8 @@ struct DevNet {
   int32_t n_vnz;           // entries in vlist
   int32_t max_vlen;        // largest number of species one reaction changes
   const int2 *rdesc;       // [M] {s0, s1}
-  const double *c;         // [M]
+  const double *c;         // [M] rates in effect (0 for forbidden channels)
+  const double *c0;        // [M] the network's rates (the gradient divides by these)
   const int32_t *vptr;     // [M+1] net change of reaction k: vlist[vptr[k]..vptr[k+1])
   const int2 *vlist;       // {species, delta}
   const int32_t *sptr;     // [N+1] reactions with species s as a reactant: slist[sptr[s]..sptr[s+1])
@@ -58,7 +62,8 @@ struct rt_network {
   int64_t n_dep_nz = 0;
   // host copies used by the batched mode's packer
   std::string host_blob;  // the arena's bytes
-  size_t off_rdesc = 0, off_c = 0, off_vptr = 0, off_vlist = 0, off_sptr = 0, off_slist = 0, off_dep = 0;
+  size_t off_rdesc = 0, off_c = 0, off_c0 = 0, off_vptr = 0, off_vlist = 0, off_sptr = 0, off_slist = 0, off_dep = 0;
+  std::vector<double> c_host;  // the network's rates (host copy)
   size_t off_depw = 0, off_depw16 = 0, off_depw8 = 0;
   size_t off_vpack = 0;
   rt::SmallNet small = {};  // filled when M <= kSmallM and N <= kSmallN

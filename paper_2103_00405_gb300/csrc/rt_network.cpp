@@ -209,6 +209,7 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
   size_t off = 0;
   g->off_rdesc = off; off = align_up(off + sizeof(int2) * M, 256);
   g->off_c = off; off = align_up(off + sizeof(double) * M, 256);
+  g->off_c0 = off; off = align_up(off + sizeof(double) * M, 256);
   g->off_vptr = off; off = align_up(off + sizeof(int32_t) * (M + 1), 256);
   g->off_vlist = off; off = align_up(off + sizeof(int2) * std::max<size_t>(1, vlist.size()), 256);
   g->off_sptr = off; off = align_up(off + sizeof(int32_t) * (N + 1), 256);
@@ -223,6 +224,8 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
   char *hb = &g->host_blob[0];
   memcpy(hb + g->off_rdesc, rdesc.data(), sizeof(int2) * M);
   memcpy(hb + g->off_c, cc.data(), sizeof(double) * M);
+  memcpy(hb + g->off_c0, cc.data(), sizeof(double) * M);
+  g->c_host = cc;
   memcpy(hb + g->off_vptr, vptr.data(), sizeof(int32_t) * (M + 1));
   if (!vlist.empty()) memcpy(hb + g->off_vlist, vlist.data(), sizeof(int2) * vlist.size());
   memcpy(hb + g->off_sptr, sptr.data(), sizeof(int32_t) * (N + 1));
@@ -254,6 +257,7 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
   d.max_vlen = max_vlen;
   d.rdesc = (const int2 *)(db + g->off_rdesc);
   d.c = (const double *)(db + g->off_c);
+  d.c0 = (const double *)(db + g->off_c0);
   d.vptr = (const int32_t *)(db + g->off_vptr);
   d.vlist = (const int2 *)(db + g->off_vlist);
   d.sptr = (const int32_t *)(db + g->off_sptr);
@@ -294,5 +298,24 @@ extern "C" int rt_network_info(const rt_network *g, int32_t *n_species, int32_t 
   if (n_reactions) *n_reactions = g->dev.M;
   if (max_dependents) *max_dependents = g->max_dependents;
   if (n_dependency_nz) *n_dependency_nz = g->n_dep_nz;
+  return RT_OK;
+}
+
+extern "C" int rt_network_set_enabled(rt_network *g, const uint8_t *enabled) {
+  clear_error();
+  if (!g) return set_error(RT_ERR_INVALID_ARG, "rt_network_set_enabled: NULL network");
+  const int32_t M = g->dev.M;
+  std::vector<double> eff(g->c_host);
+  if (enabled)
+    for (int32_t k = 0; k < M; k++)
+      if (!enabled[k]) eff[k] = 0.0;
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != g->device) return set_error(RT_ERR_INVALID_ARG, "network lives on device %d, device %d is current", g->device, dev);
+  const cudaError_t e = cudaMemcpy((char *)g->arena + g->off_c, eff.data(), sizeof(double) * M, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return set_error(RT_ERR_CUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+  memcpy(&g->host_blob[0] + g->off_c, eff.data(), sizeof(double) * M);
+  if (g->small.ok)
+    for (int32_t k = 0; k < M; k++) g->small.c[k] = eff[k];
   return RT_OK;
 }

@@ -13,6 +13,10 @@ In the absolute-time form (mode 1):
  16 dependency test reads only a reaction's first reactant species
  17 absolute firing time computed without the update time (a relative waiting time)
  18 internal times not brought up to the end of the run
+In Table 3's rescaled form (mode 2):
+ 19 waiting times shifted by dt but not rescaled by p_k / a_k
+ 20 the fired channel's new waiting time reuses its previous draw
+ 21 a frozen channel's remaining internal time lost when it resumes
 The pin suite (tests/test_oracle_pins.py) must fail on every one of them.
 """
 import concurrent.futures
@@ -25,7 +29,7 @@ import pytest
 import oracle
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-MUTANTS = list(range(1, 19))
+MUTANTS = list(range(1, 22))
 
 
 def _run_pins(n, tmpdir):

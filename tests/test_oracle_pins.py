@@ -26,7 +26,7 @@ import scipy.stats
 import oracle
 from paper_2103_00405_gb300 import workloads as W
 
-MODES = [oracle.MODE_EAGER, oracle.MODE_LAZY]
+MODES = [oracle.MODE_EAGER, oracle.MODE_LAZY, oracle.MODE_RESCALED]
 
 
 def _run(mode, *args, **kw):
@@ -470,19 +470,21 @@ def test_grid_length_rule():
 # ----------------------------------------------------------------------------------
 
 
+@pytest.mark.parametrize("mode", [oracle.MODE_LAZY, oracle.MODE_RESCALED])
 @pytest.mark.parametrize("seed", [1, 2, 3, 4])
-def test_lazy_form_follows_the_same_path_as_table_2(seed, nthreads):
-    """The two forms are the same method in exact arithmetic: on random uni/bimolecular networks
-    the event streams agree (channel by channel) and the times to within rounding, as long as no
-    two channels are within rounding of a tie.  A channel left stale (not touched although it
-    reads a changed species, or its internal time not brought up to the event) changes the path
-    within a few events."""
+def test_other_forms_follow_the_same_path_as_table_2(seed, mode, nthreads):
+    """The absolute-time form and Table 3's rescaled form are the same method as Table 2's
+    internal-time form in exact arithmetic: on random uni/bimolecular networks the event streams
+    agree (channel by channel) and the times to within rounding, as long as no two channels are
+    within rounding of a tie.  A channel left stale (not touched although it reads a changed
+    species, its internal time not brought up to the event, a waiting time not rescaled, a
+    frozen remaining internal time lost) changes the path within a few events."""
     net = W.random_mass_action(8, 40, seed=300 + seed, c_sigma=0.8)
     x0 = W.poisson_x0(8, 25, seed)
     K = 400
     e = oracle.run(net, x0, math.inf, 64, seed=seed, max_events=K, want_grad=True, trace_len=K, n_threads=nthreads)
     z = oracle.run(net, x0, math.inf, 64, seed=seed, max_events=K, want_grad=True, trace_len=K, n_threads=nthreads,
-                   mode=oracle.MODE_LAZY)
+                   mode=mode)
     same = (e["trace_mu"] == z["trace_mu"]).all(1)
     assert same.mean() >= 0.95, same.mean()
     assert (e["trace_mu"][:, 0] == z["trace_mu"][:, 0]).all()  # the first event is computed identically
@@ -515,3 +517,15 @@ def test_forbidden_channel_is_frozen(mode, nthreads):
     for k in ("t_last", "t_internal", "loglik", "trace_t"):
         assert np.array_equal(f[k].view(np.int64), z[k].view(np.int64)), k
     assert (f["counts"][:, en == 0] == 0).all()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_frozen_channel_resumes_with_its_remaining_internal_time(mode):
+    """A channel whose propensity drops to 0 and comes back keeps its unused internal time
+    (Table 2's refresh rule; Table 3 with the frozen-channel reading): A -> B, B -> A at rates
+    making the reverse channel switch on and off, against Table 2's form event by event."""
+    net = W.isomerisation(3.0, 1.0)
+    e = oracle.run(net, [1, 0], 20.0, 200, seed=7, trace_len=400)
+    z = _run(mode, net, [1, 0], 20.0, 200, seed=7, trace_len=400)
+    assert (e["trace_mu"] == z["trace_mu"]).mean() > 0.99
+    np.testing.assert_allclose(z["trace_t"], e["trace_t"], rtol=1e-10, atol=1e-12)
