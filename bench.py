@@ -18,6 +18,8 @@ their own disjoint blocks), and the int64 moment sums are all-reduced over ranks
              (FP64-issue roofline), against one launch per network on a 512-network subset
   grad    -- M = 64, N = 16, 65536 trajectories to t_end = 5, forward with the
              log-likelihood + backward kernel (FP64-issue roofline), against the plain forward
+  table3  -- the paper's own Table 3 formulation against Table 2's internal-time form on the
+             Lotka-Volterra model of Fig. 1, 2^18 trajectories to t_end = 10
 
 Printed JSON: value = events/s of the whole job (sum over ranks of fired events / max
 over ranks of the timed device time); e2e = the same metric through api.simulate with
@@ -70,7 +72,8 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="all", choices=["all", "ensemble", "large", "large_tree", "batched", "grad"],
+    ap.add_argument("--workload", default="all",
+                    choices=["all", "ensemble", "large", "large_tree", "batched", "grad", "table3"],
                     help="all (default): the ensemble headline plus the large, batched and grad sub-records; "
                          "one name: that workload alone as the line's headline (profiling captures)")
     ap.add_argument("--traj", type=int, default=1 << 20, help="ensemble: trajectories per network per step")
@@ -613,6 +616,48 @@ def run_large_tree(args, ctx, steps, warmup):
                                  "~1/100 of the internal-time scan's 32 MB"}}
 
 
+def run_table3(args, ctx, steps, warmup):
+    """The paper's own GPU formulation (Table 3: relative waiting times rescaled after every
+    event, every propensity recomputed) against Table 2's internal-time form, on the model of the
+    paper's Fig. 1 (Lotka-Volterra, Table 4 rates, X0 = Y0 = 1000), 2^18 trajectories to t_end = 10
+    per step, one thread per trajectory, the same trajectories both ways."""
+    import torch
+
+    from paper_2103_00405_gb300 import _lib as L
+    from paper_2103_00405_gb300 import api
+
+    n = 1 << 18
+    cfg = W.ensemble_configs(n)[0]
+    netg = api.Network(cfg["net"])
+    x0 = torch.as_tensor(cfg["x0"], dtype=torch.int32).to(ctx.dev)
+    res = {}
+    for name, form in (("table3_rescaled", L.RT_FORM_RESCALED), ("table2_internal", L.RT_FORM_INTERNAL)):
+        outs = {}
+        step_events = []
+
+        def step(i, record):
+            outs.update(api.simulate(netg, x0, cfg["t_end"], n, seed=1, traj_offset=traj_base(ctx.rank, i, n),
+                                     max_events=cfg["max_events"], mapping=L.RT_MAP_THREAD, form=form,
+                                     outputs=outs))
+
+        ms, _, clocks = timed_steps(ctx, step, steps, warmup,
+                                    after=lambda i: step_events.append(int(outs["n_events"].sum().item())))
+        dev_ms, events_all = combine_over_ranks(sum(ms), sum(step_events), ctx.world, ctx.dev)
+        res[name] = {"value": events_all / (dev_ms / 1e3), "unit": UNIT, "ms_per_step": dev_ms / steps,
+                     "events_per_step": events_all / steps, "clocks": clocks,
+                     "kernel": "k_ens_rescaled<3,false,true>" if form == L.RT_FORM_RESCALED
+                     else "k_ens_small<3,2,false>"}
+    line = {"value": res["table3_rescaled"]["value"], "unit": UNIT, "steps": steps, "warmup": warmup,
+            "ms_per_step": res["table3_rescaled"]["ms_per_step"],
+            "config": {"workload": "Table 3's form vs Table 2's internal-time form: Lotka-Volterra (Fig. 1 model, "
+                                   "Table 4 rates, X0=Y0=1000), 2^18 trajectories to t_end=10 per step, one thread "
+                                   "per trajectory, the same trajectories both ways",
+                       "parallelism": "trajectories sharded over ranks" if ctx.world > 1 else "1 GPU"},
+            "gpu_launches": steps, "forms": res,
+            "internal_over_rescaled": res["table2_internal"]["value"] / res["table3_rescaled"]["value"]}
+    return line
+
+
 # ----------------------------------------------------------------------------------------
 # Batched
 # ----------------------------------------------------------------------------------------
@@ -784,9 +829,11 @@ def main(argv=None):
         line = run_ensemble(args, ctx)
         if args.workload == "all":
             line["workloads"] = {"large": run_large(args, ctx, **sub), "large_tree": run_large_tree(args, ctx, **sub),
-                                 "batched": run_batched(args, ctx, **sub), "grad": run_grad(args, ctx, **sub)}
+                                 "batched": run_batched(args, ctx, **sub), "grad": run_grad(args, ctx, **sub),
+                                 "table3": run_table3(args, ctx, **sub)}
     else:
-        fn = {"large": run_large, "large_tree": run_large_tree, "batched": run_batched, "grad": run_grad}[args.workload]
+        fn = {"large": run_large, "large_tree": run_large_tree, "batched": run_batched, "grad": run_grad,
+              "table3": run_table3}[args.workload]
         rec = fn(args, ctx, args.steps, args.warmup)
         line = {"metric": METRIC, "value": rec.pop("value"), "unit": UNIT, "n_gpus": ctx.world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": rec.pop("ms_per_step"), "higher_is_better": True,

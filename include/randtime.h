@@ -75,13 +75,19 @@ enum {
 enum {
   RT_FORM_INTERNAL = 0, /* Table 2 in internal times: every T_k advanced at every event,
                            T_k += a_k dt, waiting times (P_k - T_k) / a_k for all k */
-  RT_FORM_ABSOLUTE = 1  /* absolute firing times with the dependency graph (Sec. 5): channel k
+  RT_FORM_ABSOLUTE = 1, /* absolute firing times with the dependency graph (Sec. 5): channel k
                            keeps s_k (real time of its last update) and
                            tau_k = s_k + (P_k - T_k) / a_k; an event at t = tau_mu touches only
                            mu and the channels reading a changed species:
                            T_k += a_k (t - s_k), s_k = t, P_mu += E, a_k and tau_k recomputed;
                            at the end T_k += a_k (t_f - s_k) with t_f = t_end (run reached it)
                            or the last event time */
+  RT_FORM_RESCALED = 2  /* Table 3's form (thread mapping, M <= 8): relative waiting times w_k;
+                           after an event that took dt every propensity is recomputed and every
+                           other waiting time rescaled, w_k = (p_k / a_k)(w_k - dt), p_k the
+                           previous propensity; the fired channel draws w_mu = E / a_mu; a channel
+                           whose propensity is 0 keeps its remaining internal time p_k (w_k - dt)
+                           frozen and resumes with w_k = q_k / a_k; T_k += a_k dt per event */
 };
 
 typedef struct rt_network rt_network;

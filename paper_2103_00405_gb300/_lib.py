@@ -19,7 +19,7 @@ i32, u32, i64, u64, dbl, vp, sz = (ctypes.c_int32, ctypes.c_uint32, ctypes.c_int
 RT_OK, RT_ERR_INVALID_ARG, RT_ERR_UNSUPPORTED, RT_ERR_CUDA, RT_ERR_OOM, RT_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 RT_TRAJ_TEND, RT_TRAJ_MAX_EVENTS, RT_TRAJ_ABSORBED, RT_TRAJ_OVERFLOW, RT_TRAJ_TIMEOUT, RT_TRAJ_BAD_X0 = range(6)
 RT_MAP_AUTO, RT_MAP_THREAD, RT_MAP_WARP, RT_MAP_BLOCK, RT_MAP_BUNDLE, RT_MAP_TREE = -1, 0, 1, 2, 3, 4
-RT_FORM_INTERNAL, RT_FORM_ABSOLUTE = 0, 1
+RT_FORM_INTERNAL, RT_FORM_ABSOLUTE, RT_FORM_RESCALED = 0, 1, 2
 
 
 class rt_launch_cfg(ctypes.Structure):

@@ -19,6 +19,7 @@ int check_device(const rt_network *net) {
 static int choose_mapping(const rt_network *net, const rt_launch_cfg *cfg, int form = RT_FORM_INTERNAL) {
   if (cfg && cfg->mapping != RT_MAP_AUTO) return cfg->mapping;
   if (form == RT_FORM_ABSOLUTE) return RT_MAP_TREE;
+  if (form == RT_FORM_RESCALED) return RT_MAP_THREAD;
   if (net->dev.M <= thread_mapping_max_m()) return RT_MAP_THREAD;
   if (net->dev.M <= warp_mapping_max_m()) return RT_MAP_WARP;
   if (net->dev.M <= block_mapping_max_m()) return RT_MAP_BLOCK;
@@ -41,8 +42,8 @@ int validate_run(const rt_network *net, const rt_run_params *p, const rt_outputs
   if ((o->grid_sumsq_dev || o->grid_count_dev) && !o->grid_sum_dev)
     return set_error(RT_ERR_INVALID_ARG, "grid_sumsq/grid_count need grid_sum");
   if (o->trace_len < 0) return set_error(RT_ERR_INVALID_ARG, "trace_len must be >= 0");
-  if (p->form != RT_FORM_INTERNAL && p->form != RT_FORM_ABSOLUTE)
-    return set_error(RT_ERR_INVALID_ARG, "form must be RT_FORM_INTERNAL or RT_FORM_ABSOLUTE");
+  if (p->form != RT_FORM_INTERNAL && p->form != RT_FORM_ABSOLUTE && p->form != RT_FORM_RESCALED)
+    return set_error(RT_ERR_INVALID_ARG, "form must be RT_FORM_INTERNAL, RT_FORM_ABSOLUTE or RT_FORM_RESCALED");
   return RT_OK;
 }
 
@@ -94,6 +95,10 @@ extern "C" int rt_run(const rt_network *net, const rt_run_params *p, const rt_ou
   if ((p->form == RT_FORM_ABSOLUTE) != (mapping == RT_MAP_TREE))
     return set_error(RT_ERR_UNSUPPORTED, "the absolute-time form runs on the tree mapping (RT_MAP_TREE) and the "
                      "tree mapping runs the absolute-time form only");
+  if (p->form == RT_FORM_RESCALED) {
+    if (mapping != RT_MAP_THREAD) return set_error(RT_ERR_UNSUPPORTED, "Table 3's rescaled form runs on the thread mapping");
+    return launch_rescaled_mapping(a, B, s);
+  }
   switch (mapping) {
     case RT_MAP_THREAD:
       // networks of <= 4 reactions and <= 4 species: network in the parameter space, X in registers

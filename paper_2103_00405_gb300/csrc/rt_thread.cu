@@ -74,4 +74,62 @@ int launch_thread_mapping(const RunArgs &a, int B, cudaStream_t s) {
   return RT_OK;
 }
 
+// ---------------------------------------------------------------------------------
+// Table 3's rescaled form (RT_FORM_RESCALED), one thread per trajectory, M <= 8.
+// ---------------------------------------------------------------------------------
+template <int MAXM, bool LL, bool EXACT>
+__global__ void __launch_bounds__(128, EXACT ? 8 : 4)
+    k_ens_rescaled(const RunArgs A, const int tend_finite, const int mom_cl, const int want_T) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int M = A.net.M, N = A.net.N, nv = A.net.n_vnz;
+  ThreadNet S = carve_thread_net(smem, M, nv, N, blockDim.x);
+  const int smem_mom = mom_cl > 0 ? 1 : 0;
+  S.mt = mom_table(S.mom, A.G, mom_cl);
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    S.c[i] = A.net.c[i];
+    S.dep[i] = A.net.depmask[i];
+    S.rd[i] = A.net.rdesc[i];
+  }
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) S.vl[i] = A.net.vlist[i];
+  for (int i = threadIdx.x; i <= M; i += blockDim.x) S.vp[i] = A.net.vptr[i];
+  if (smem_mom) mom_zero_and_sync(S.mt, N);
+  else __syncthreads();
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < A.n_traj) simulate_rescaled<MAXM, LL, EXACT>(A, S, j, blockDim.x, tend_finite, smem_mom, want_T);
+  if (smem_mom) mom_sync_and_flush(S.mt, A);
+}
+
+template <int MAXM, bool EXACT = false>
+static cudaError_t launch_rescaled_m(const RunArgs &a, int B, cudaStream_t s, int tend_finite) {
+  const int cl = moment_cluster(a);
+  const size_t mom = cl ? moment_share_bytes(a, cl) : 0;
+  const size_t smem = ((thread_smem_bytes(a.net.M, a.net.N, a.net.n_vnz, B) + 7) & ~(size_t)7) + mom;
+  unsigned grid = (unsigned)((a.n_traj + B - 1) / B);
+  if (cl > 1) grid = (grid + cl - 1) / cl * cl;
+  const int want_T = (a.out.loglik_dev || a.out.t_internal_dev) ? 1 : 0;
+  auto kern = a.out.loglik_dev ? k_ens_rescaled<MAXM, true, EXACT> : k_ens_rescaled<MAXM, false, EXACT>;
+  return launch_clustered(kern, grid, B, smem, s, cl, a, tend_finite, cl, want_T);
+}
+
+int launch_rescaled_mapping(const RunArgs &a, int B, cudaStream_t s) {
+  if (a.n_traj == 0) return RT_OK;
+  if (B <= 0) B = 128;
+  if (B > 128 || B % 32) return set_error(RT_ERR_INVALID_ARG, "thread mapping: block_threads must be a multiple of 32 <= 128");
+  if (a.net.M > 8 || !a.net.depmask)
+    return set_error(RT_ERR_UNSUPPORTED, "Table 3's rescaled form runs on the thread mapping with M <= 8 (got %d)", a.net.M);
+  if (thread_smem_bytes(a.net.M, a.net.N, a.net.n_vnz, B) > 200 * 1024)
+    return set_error(RT_ERR_UNSUPPORTED, "thread mapping: network too large for shared memory");
+  const int tf = isfinite(a.t_end) ? 1 : 0;
+  cudaError_t e;
+  switch (a.net.M) {
+    case 1: e = launch_rescaled_m<1, true>(a, B, s, tf); break;
+    case 2: e = launch_rescaled_m<2, true>(a, B, s, tf); break;
+    case 3: e = launch_rescaled_m<3, true>(a, B, s, tf); break;
+    case 4: e = launch_rescaled_m<4, true>(a, B, s, tf); break;
+    default: e = launch_rescaled_m<8>(a, B, s, tf); break;
+  }
+  if (e != cudaSuccess) return set_error(RT_ERR_CUDA, "rescaled-form kernel launch: %s", cudaGetErrorString(e));
+  return RT_OK;
+}
+
 }  // namespace rt

@@ -1,0 +1,76 @@
+"""Table 3's form of the method (relative waiting times rescaled by p_k / a_k after every event,
+every propensity recomputed; RT_FORM_RESCALED on the thread mapping) against the oracle's mode 2,
+bit for bit, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2103_00405_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("CUDA not available", allow_module_level=True)
+
+from paper_2103_00405_gb300 import _lib as L  # noqa: E402
+from paper_2103_00405_gb300 import api  # noqa: E402
+from paper_2103_00405_gb300 import build as B  # noqa: E402
+
+from test_gpu_parity import assert_same  # noqa: E402
+from test_gpu_trace import assert_trace  # noqa: E402
+
+B.build()
+
+RES = dict(form=L.RT_FORM_RESCALED)
+MODE = dict(mode=oracle.MODE_RESCALED)
+
+CASES = {
+    "lotka_volterra": (W.lotka_volterra(), np.array([1000, 1000], np.int32), 1.0),
+    "birth_death": (W.birth_death(), np.array([0], np.int32), 10.0),
+    "dimerisation": (W.dimerisation(), np.array([1000, 0], np.int32), 5.0),
+    "isomerisation_frozen": (W.isomerisation(3.0, 1.0), np.array([1, 0], np.int32), 20.0),
+    "random_8": (W.random_mass_action(6, 8, seed=91), None, 0.5),
+    "random_5": (W.random_mass_action(4, 5, seed=92), None, 0.5),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rescaled_form_bit_exact(name):
+    net, x0, t_end = CASES[name]
+    if x0 is None:
+        x0 = W.poisson_x0(net.n_species, 30, 3)
+    n = 200
+    netg = api.Network(net)
+    g = api.simulate(netg, x0, t_end, n, seed=2, stream_id=1, traj_offset=17, max_events=200000, grad=True,
+                     grid="traj", sample_dt=t_end / 20, trace_len=500, **RES)
+    o = oracle.run(net, x0, t_end, n, seed=2, stream_id=1, traj_offset=17, max_events=200000, want_grad=True,
+                   want_grid=True, sample_dt=t_end / 20, trace_len=500, n_threads=16, **MODE)
+    assert_same(g, o)
+    assert_trace(g, o)
+
+
+def test_rescaled_form_moments_and_absorption():
+    net, x0 = W.dimerisation(), np.array([1000, 0], np.int32)
+    netg = api.Network(net)
+    g = api.simulate(netg, x0, 2.0, 3000, seed=5, sample_dt=0.1, grid="moments", **RES)
+    o = oracle.run(net, x0, 2.0, 3000, seed=5, sample_dt=0.1, want_grid=True, n_threads=16, **MODE)
+    grid = o["grid"].astype(np.int64)
+    assert np.array_equal(g["grid_sum"].cpu().numpy(), grid.sum(0))
+    assert np.array_equal(g["grid_sumsq"].cpu().numpy(), (grid ** 2).sum(0))
+    death = W._from_lists(1, [({0: 1}, {}, 1.0)], "death")
+    gd = api.simulate(api.Network(death), np.array([[5], [-1]], np.int32), math.inf, 2, seed=1, grad=True, **RES)
+    od = oracle.run(death, np.array([[5], [-1]], np.int32), math.inf, 2, seed=1, want_grad=True, **MODE)
+    assert od["status"].tolist() == [oracle.ST_ABSORBED, oracle.ST_BAD_X0]
+    assert_same(gd, od)
+
+
+def test_rescaled_form_limits():
+    netg = api.Network(W.random_mass_action(6, 12, seed=93))
+    with pytest.raises(L.RandtimeError):
+        api.simulate(netg, W.poisson_x0(6, 10, 1), 1.0, 4, **RES)  # M > 8
+    with pytest.raises(L.RandtimeError):
+        api.simulate(api.Network(W.birth_death()), [0], 1.0, 4, mapping=L.RT_MAP_WARP, **RES)
