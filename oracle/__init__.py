@@ -57,7 +57,7 @@ def _declare(lib):
     lib.oracle_uniform.restype = dbl
     lib.oracle_grid_len.argtypes = [dbl, dbl]
     lib.oracle_grid_len.restype = i64
-    lib.oracle_run.argtypes = [i32, i32, i32, i64, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, i32,
+    lib.oracle_run.argtypes = [i32, i32, i32, i64, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, i32,
                                dbl, i64, u64, u32, i64, i64, dbl,
                                vp, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, i32]
     lib.oracle_run.restype = ctypes.c_int
@@ -112,13 +112,14 @@ MODE_EAGER, MODE_LAZY, MODE_RESCALED = 0, 1, 2
 
 def run(net, x0, t_end, n_traj, seed=1, stream_id=0, traj_offset=0, max_events=(1 << 31) - 1,
         sample_dt=0.0, want_grid=False, want_grad=False, trace_len=0, n_threads=1, lib=None,
-        mode=MODE_EAGER, enabled=None):
+        mode=MODE_EAGER, enabled=None, beta=None):
     """Run the oracle; returns a dict of numpy arrays.
 
     x0 is [N] (shared) or [n_traj, N] (per trajectory).  mode: MODE_EAGER (Table 2 in
     internal-time form), MODE_LAZY (absolute-time form with the dependency graph) or
     MODE_RESCALED (Table 3's rescaled waiting times, every propensity recomputed).
     enabled: optional [M] flags; channels with 0 never fire (frozen internal time).
+    beta: optional [M] rate slopes, c_k(t) = c_k (1 + beta_k t), beta_k >= 0 (mode 0 only).
     """
     lib = lib or load()
     N, M = int(net.n_species), int(net.n_reactions)
@@ -144,9 +145,12 @@ def run(net, x0, t_end, n_traj, seed=1, stream_id=0, traj_offset=0, max_events=(
     en = None if enabled is None else np.ascontiguousarray(enabled, dtype=np.uint8)
     if en is not None and en.shape != (M,):
         raise ValueError("enabled must have one entry per reaction")
+    bt = None if beta is None else np.ascontiguousarray(beta, dtype=np.float64)
+    if bt is not None and bt.shape != (M,):
+        raise ValueError("beta must have one entry per reaction")
     rc = lib.oracle_run(int(mode), N, M, len(net.reac_rxn), _p(net.reac_rxn), _p(net.reac_sp), _p(net.reac_coef),
                         len(net.stoi_rxn), _p(net.stoi_rxn), _p(net.stoi_sp), _p(net.stoi_delta),
-                        _p(net.c), _p(en), _p(x0), per, float(t_end), int(max_events), int(seed), int(stream_id),
+                        _p(net.c), _p(en), _p(bt), _p(x0), per, float(t_end), int(max_events), int(seed), int(stream_id),
                         n_traj, int(traj_offset), float(sample_dt),
                         _p(out["x_final"]), _p(out.get("grid")), _p(out["n_events"]), _p(out["status"]),
                         _p(out["t_last"]), _p(out.get("loglik")), _p(out.get("counts")),

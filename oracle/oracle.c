@@ -55,6 +55,15 @@
  *      internal time q_k = p_k (w_k - dt) frozen (w_k = +inf) and resumes with
  *      w_k = q_k / a_k.  Internal times for the likelihood accumulate T_k += a_k dt.
  *      Same path as modes 0 and 1 in exact arithmetic.
+ * beta (NULL = constant rates; mode 0 only): time-dependent rates c_k(t) = c_k (1 + beta_k t),
+ * beta_k >= 0 (Sec. 6, Eq. 29: the random-time form needs only each channel's own
+ * integral).  With A_k = c_k h_k(X) constant between events, channel k's internal time
+ * over [t, t + d] grows by A_k I_k(t, d), I_k = d (1 + beta_k t) + beta_k d^2 / 2, and its
+ * waiting time solves A_k I_k(t, d) = P_k - T_k:
+ *   u = 1 + beta t,  b = A u,  d = 2 R / (b + sqrt(b^2 + 2 A beta R)),  R = P_k - T_k
+ * (the root of the quadratic written without cancellation); for beta_k = 0 the operations
+ * are exactly those of the constant-rate form.  ln a_mu is taken at the event time,
+ * a_mu = A_mu (1 + beta_mu t).
  * enabled (NULL = all): a channel with enabled[k] == 0 is forbidden to fire; its
  * propensity is taken as 0, so its internal time is frozen (Table 2's note on
  * boundary conditions).
@@ -249,6 +258,7 @@ typedef struct {
   int32_t *vsp, *vdel;
   const double *c;
   const uint8_t *enabled; /* NULL: every channel may fire */
+  const double *beta;     /* NULL: constant rates; else c_k (1 + beta_k t) */
 } onet;
 
 /* Group COO entries by reaction; entries for the same (reaction, species) are summed
@@ -320,6 +330,25 @@ static double propensity(const onet *g, int32_t k, const int32_t *X) {
 
 enum { ST_TEND = 0, ST_MAX_EVENTS = 1, ST_ABSORBED = 2, ST_OVERFLOW = 3, ST_BAD_X0 = 5 };
 
+/* Waiting time of a channel with base propensity A > 0, rate slope beta and remaining internal
+ * time R at time t (Eq. 29 for c(t) = c (1 + beta t)). */
+static double tdep_wait(double A, double beta, double R, double t) {
+  if (!(R > 0.0)) return 0.0;
+  if (beta == 0.0) return R / A;
+  double u = 1.0 + (ORACLE_MUTANT == 23 ? 0.0 : beta * t);
+  double b = A * u;
+  double e = ((2.0 * A) * beta) * R;
+  double den = b + sqrt(b * b + e);
+  return (2.0 * R) / den;
+}
+
+/* int_t^{t+d} (1 + beta s) ds = d (1 + beta t) + beta d^2 / 2 */
+static double tdep_integral(double beta, double t, double d) {
+  if (beta == 0.0) return d;
+  double u = 1.0 + beta * t;
+  return d * u + (ORACLE_MUTANT == 22 ? 0.0 : ((beta * d) * d) * 0.5);
+}
+
 int64_t oracle_grid_len(double t_end, double sample_dt) {
   if (!(sample_dt > 0.0) || !isfinite(t_end) || t_end < 0.0) return 0;
   return (int64_t)floor(t_end / sample_dt * (1.0 + 1e-12)) + 1;
@@ -382,6 +411,8 @@ static void run_traj(const job_t *J, int64_t j, double *P, double *T, double *a,
         double w;
         if (a[k] == 0.0) {
           w = INFINITY;
+        } else if (g->beta) {
+          w = tdep_wait(a[k], g->beta[k], P[k] - T[k], t);
         } else {
           double rem = P[k] - (ORACLE_MUTANT == 3 ? 0.0 : T[k]);
           w = rem > 0.0 ? rem / a[k] : 0.0;
@@ -409,6 +440,7 @@ static void run_traj(const job_t *J, int64_t j, double *P, double *T, double *a,
       else
         while (gi < J->G && (double)gi * J->sample_dt < tn) gi++;
 
+      double tprev = t;
       t = tn;
       /* every internal time advances by a_k dt (Eq. 17) */
       if (ORACLE_MUTANT == 5) { /* propensities of the post-event state used for the elapsed step */
@@ -416,8 +448,15 @@ static void run_traj(const job_t *J, int64_t j, double *P, double *T, double *a,
         for (int32_t k = 0; k < M; k++) a[k] = propensity(g, k, X);
         for (int64_t i = g->vptr[mu]; i < g->vptr[mu + 1]; i++) X[g->vsp[i]] -= g->vdel[i];
       }
-      for (int32_t k = 0; k < M; k++) T[k] = T[k] + a[k] * (ORACLE_MUTANT == 6 ? t : dmin);
-      if (J->loglik) ll = ll + oracle_rt_log(a[mu]);
+      if (g->beta) {
+        /* over the step [tprev, t]: int c_k(s) h_k ds = A_k I_k(tprev, dt) */
+        for (int32_t k = 0; k < M; k++) T[k] = T[k] + a[k] * tdep_integral(g->beta[k], tprev, dmin);
+        if (J->loglik)
+          ll = ll + oracle_rt_log(a[mu] * (1.0 + g->beta[mu] * (ORACLE_MUTANT == 24 ? tprev : t)));
+      } else {
+        for (int32_t k = 0; k < M; k++) T[k] = T[k] + a[k] * (ORACLE_MUTANT == 6 ? t : dmin);
+        if (J->loglik) ll = ll + oracle_rt_log(a[mu]);
+      }
       /* fire: X += v_mu (Eq. 5) */
       for (int64_t i = g->vptr[mu]; i < g->vptr[mu + 1]; i++)
         X[g->vsp[i]] += (ORACLE_MUTANT == 7 && g->vdel[i] < 0) ? -g->vdel[i] : g->vdel[i];
@@ -442,7 +481,8 @@ static void run_traj(const job_t *J, int64_t j, double *P, double *T, double *a,
   if (status != ST_BAD_X0 && (status == ST_TEND || status == ST_ABSORBED) && isfinite(J->t_end)) {
     /* internal times at t_end (for the likelihood) */
     double rest = J->t_end - t;
-    for (int32_t k = 0; k < M; k++) T[k] = T[k] + a[k] * rest;
+    for (int32_t k = 0; k < M; k++)
+      T[k] = T[k] + a[k] * (g->beta ? tdep_integral(g->beta[k], t, rest) : rest);
   }
   if (J->loglik) {
     /* log-likelihood of the path: sum of ln a_mu minus the integrated propensity */
@@ -724,20 +764,25 @@ static void *worker(void *arg) {
 int oracle_run(int32_t mode, int32_t N, int32_t M,
                int64_t n_reac_nz, const int32_t *reac_rxn, const int32_t *reac_sp, const int32_t *reac_coef,
                int64_t n_stoi_nz, const int32_t *stoi_rxn, const int32_t *stoi_sp, const int32_t *stoi_delta,
-               const double *c, const uint8_t *enabled, const int32_t *x0, int32_t per_traj_x0,
+               const double *c, const uint8_t *enabled, const double *beta, const int32_t *x0, int32_t per_traj_x0,
                double t_end, int64_t max_events, uint64_t seed, uint32_t stream,
                int64_t n_traj, int64_t traj_offset, double sample_dt,
                int32_t *x_final, int32_t *grid, int64_t *n_events, int32_t *status, double *t_last,
                double *loglik, int32_t *counts, double *t_internal,
                int64_t trace_len, int32_t *trace_mu, double *trace_t, int32_t n_threads) {
   if (mode < 0 || mode > 2 || N < 1 || M < 1 || n_traj < 0 || max_events < 0 || t_end != t_end) return -1;
+  if (beta) {
+    if (mode != 0) return -1;
+    for (int32_t k = 0; k < M; k++)
+      if (!(beta[k] >= 0.0) || !isfinite(beta[k])) return -1;
+  }
   for (int64_t i = 0; i < n_reac_nz; i++)
     if (reac_rxn[i] < 0 || reac_rxn[i] >= M || reac_sp[i] < 0 || reac_sp[i] >= N || reac_coef[i] <= 0)
       return -1;
   for (int64_t i = 0; i < n_stoi_nz; i++)
     if (stoi_rxn[i] < 0 || stoi_rxn[i] >= M || stoi_sp[i] < 0 || stoi_sp[i] >= N) return -1;
   onet g;
-  g.N = N; g.M = M; g.c = c; g.enabled = enabled;
+  g.N = N; g.M = M; g.c = c; g.enabled = enabled; g.beta = beta;
   if (group_coo(M, n_reac_nz, reac_rxn, reac_sp, reac_coef, &g.rptr, &g.rsp, &g.rcoef)) return -4;
   if (group_coo(M, n_stoi_nz, stoi_rxn, stoi_sp, stoi_delta, &g.vptr, &g.vsp, &g.vdel)) return -4;
 

@@ -17,6 +17,10 @@ In Table 3's rescaled form (mode 2):
  19 waiting times shifted by dt but not rescaled by p_k / a_k
  20 the fired channel's new waiting time reuses its previous draw
  21 a frozen channel's remaining internal time lost when it resumes
+With time-dependent rates c_k (1 + beta_k t):
+ 22 the internal-time integral without its beta dt^2 / 2 term
+ 23 waiting times solved with the rate at time 0 instead of at the current time
+ 24 ln a_mu taken at the previous event's time
 The pin suite (tests/test_oracle_pins.py) must fail on every one of them.
 """
 import concurrent.futures
@@ -29,7 +33,7 @@ import pytest
 import oracle
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-MUTANTS = list(range(1, 22))
+MUTANTS = list(range(1, 25))
 
 
 def _run_pins(n, tmpdir):

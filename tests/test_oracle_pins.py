@@ -529,3 +529,99 @@ def test_frozen_channel_resumes_with_its_remaining_internal_time(mode):
     z = _run(mode, net, [1, 0], 20.0, 200, seed=7, trace_len=400)
     assert (e["trace_mu"] == z["trace_mu"]).mean() > 0.99
     np.testing.assert_allclose(z["trace_t"], e["trace_t"], rtol=1e-10, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------------
+# Time-dependent rates c_k(t) = c_k (1 + beta_k t)  (Sec. 6, Eq. 29)
+# ----------------------------------------------------------------------------------
+
+
+def test_zero_slopes_reproduce_constant_rates_bit_for_bit(nthreads):
+    net = W.random_mass_action(5, 9, seed=401)
+    x0 = W.poisson_x0(5, 20, 402)
+    a = oracle.run(net, x0, 1.0, 50, seed=3, want_grad=True, want_grid=True, sample_dt=0.1, trace_len=300,
+                   n_threads=nthreads)
+    b = oracle.run(net, x0, 1.0, 50, seed=3, want_grad=True, want_grid=True, sample_dt=0.1, trace_len=300,
+                   n_threads=nthreads, beta=np.zeros(9))
+    for k in a:
+        assert np.array_equal(a[k].view(np.int64) if a[k].dtype == np.float64 else a[k],
+                              b[k].view(np.int64) if b[k].dtype == np.float64 else b[k]), k
+
+
+def test_ramped_birth_is_poisson_with_the_integrated_rate(nthreads):
+    """0 -> A at c (1 + beta t): A(t) ~ Poisson(c (t + beta t^2 / 2))."""
+    c, beta, n = 20.0, 0.7, 20000
+    o = oracle.run(W.pure_birth(c), [0], 3.0, n, seed=8, sample_dt=0.5, want_grid=True, beta=[beta],
+                   n_threads=nthreads)
+    for gi, t in ((1, 0.5), (4, 2.0), (6, 3.0)):
+        lam = c * (t + beta * t * t / 2)
+        x = o["grid"][:, gi, 0]
+        assert abs(x.mean() - lam) < 4 * math.sqrt(lam / n)
+        top = int(lam + 10 * math.sqrt(lam)) + 10
+        assert _chi2_pvalue(np.bincount(x, minlength=top)[:top], scipy.stats.poisson.pmf(np.arange(top), lam)) > 1e-4
+
+
+def test_birth_death_with_ramped_immigration_solves_the_mean_equation(nthreads):
+    """0 -> A at k (1 + beta t), A -> 0 at gamma A, A(0) = 0: A(t) is Poisson with mean
+    m(t) = k/g - k b/g^2 + (k b / g) t - (k/g - k b/g^2) e^{-g t}."""
+    k, g, beta, n = 50.0, 1.0, 0.5, 20000
+    o = oracle.run(W.birth_death(k, g), [0], 4.0, n, seed=12, sample_dt=1.0, want_grid=True, beta=[beta, 0.0],
+                   n_threads=nthreads)
+    for gi in (1, 2, 4):
+        t = float(gi)
+        m = k / g - k * beta / g ** 2 + (k * beta / g) * t - (k / g - k * beta / g ** 2) * math.exp(-g * t)
+        x = o["grid"][:, gi, 0]
+        assert abs(x.mean() - m) < 4 * math.sqrt(m / n)
+        top = int(m + 10 * math.sqrt(m)) + 10
+        assert _chi2_pvalue(np.bincount(x, minlength=top)[:top], scipy.stats.poisson.pmf(np.arange(top), m)) > 1e-4
+
+
+def test_first_event_law_with_ramped_rates(nthreads):
+    """First event from t = 0: P(tau > s) = exp(-sum_k A_k (s + beta_k s^2 / 2)), channel k with
+    probability a_k(tau) / sum a(tau) given tau."""
+    net = W.random_mass_action(4, 6, seed=77, c_sigma=0.5)
+    x0 = np.array([6, 9, 4, 7], np.int32)
+    beta = np.array([0.0, 2.0, 5.0, 0.5, 1.0, 3.0])
+    n = 30000
+    o = oracle.run(net, x0, math.inf, n, seed=5, max_events=1, trace_len=1, beta=beta, n_threads=nthreads)
+    S = net.dense_reactants()
+    A = np.array([net.c[k] * np.prod([math.comb(int(x0[i]), int(S[k, i])) for i in range(4)]) for k in range(6)])
+    tau = o["trace_t"][:, 0]
+    cdf = lambda s: 1 - np.exp(-(A.sum() * s + (A * beta).sum() * s * s / 2))
+    assert scipy.stats.kstest(tau, cdf).pvalue > 1e-4
+    # channel given the time: probabilities proportional to A_k (1 + beta_k tau); chi-square on the
+    # expected counts summed over the observed times
+    mu = o["trace_mu"][:, 0]
+    p = A[None, :] * (1 + beta[None, :] * tau[:, None])
+    p /= p.sum(1, keepdims=True)
+    assert _chi2_pvalue(np.bincount(mu, minlength=6), p.sum(0) / n) > 1e-4
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_ramped_internal_times_and_likelihood_from_the_trace(seed):
+    """T_k(t_end) = int_0^T c_k (1 + beta_k s) h_k(X(s)) ds and l = sum ln a_mu(t_mu) - sum_k T_k,
+    rebuilt from the event trace with the closed-form integral of each step."""
+    net = W.random_mass_action(4, 6, seed=31 + seed, c_sigma=0.5)
+    x0 = np.array([15, 12, 9, 20], np.int32)
+    beta = np.array([0.0, 1.5, 0.3, 2.0, 0.0, 0.8])
+    T = 0.5
+    o = oracle.run(net, x0, T, 6, seed=8, want_grad=True, trace_len=20000, beta=beta)
+    S, V = net.dense_reactants(), net.dense_stoich()
+
+    def hvec(x):
+        return np.array([np.prod([math.comb(int(x[i]), int(S[k, i])) for i in range(4)]) for k in range(6)], float)
+
+    for j in range(6):
+        n = int(o["n_events"][j])
+        x = x0.astype(np.int64).copy()
+        t, ll, integ = 0.0, 0.0, np.zeros(6)
+        for e in range(n):
+            mu, te = o["trace_mu"][j, e], o["trace_t"][j, e]
+            h = hvec(x)
+            integ += net.c * h * ((te - t) + beta * (te * te - t * t) / 2)
+            ll += math.log(net.c[mu] * h[mu] * (1 + beta[mu] * te))
+            x += V[mu]
+            t = te
+        integ += net.c * hvec(x) * ((T - t) + beta * (T * T - t * t) / 2)
+        np.testing.assert_allclose(o["t_internal"][j], integ, rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(o["loglik"][j], ll - integ.sum(), rtol=1e-9, atol=1e-9)
