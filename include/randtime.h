@@ -180,6 +180,21 @@ int rt_network_info(const rt_network *net, int32_t *n_species, int32_t *n_reacti
  */
 int rt_network_set_enabled(rt_network *net, const uint8_t *enabled);
 
+/*
+ * rt_network_set_rate_slopes -- time-dependent rates c_k(t) = c_k (1 + beta_k t) (Sec. 6,
+ * Eq. 29: in the random-time form each channel needs only its own integral, here in closed
+ * form).  beta: host array [n_reactions], finite and >= 0; NULL returns to constant rates.
+ * Between events channel k's internal time grows by A_k I_k(t, dt), A_k = c_k h_k(X),
+ * I_k = dt (1 + beta_k t) + beta_k dt^2 / 2; its waiting time is the root of
+ * A_k I_k(t, dt) = P_k - T_k, dt = 2R / (b + sqrt(b^2 + 2 A_k beta_k R)) with
+ * u = 1 + beta_k t, b = A_k u, R = P_k - T_k (for beta_k = 0: R / A_k, the constant-rate
+ * operations); ln a_mu is taken at the event time.  The gradient (n_k - T_k) / c_k keeps
+ * its form.  Networks with slopes run the internal-time form on the thread mapping
+ * (M <= 16); other mappings and batches return RT_ERR_UNSUPPORTED.  Copies to the
+ * device synchronously; no work using the network may be in flight.
+ */
+int rt_network_set_rate_slopes(rt_network *net, const double *beta);
+
 /* Number of grid points on [0, t_end] for spacing sample_dt:
  * floor(t_end / sample_dt * (1 + 1e-12)) + 1, or 0 if sample_dt <= 0 or t_end is not finite. */
 int64_t rt_grid_len(double t_end, double sample_dt);

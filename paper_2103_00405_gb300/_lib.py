@@ -63,6 +63,7 @@ SIGNATURES = [
     ("rt_network_destroy", None, [vp]),
     ("rt_network_info", ctypes.c_int, [vp, vp, vp, vp, vp]),
     ("rt_network_set_enabled", ctypes.c_int, [vp, vp]),
+    ("rt_network_set_rate_slopes", ctypes.c_int, [vp, vp]),
     ("rt_model_parse", ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.POINTER(rt_model))]),
     ("rt_model_free", None, [ctypes.POINTER(rt_model)]),
     ("rt_grid_len", i64, [dbl, dbl]),

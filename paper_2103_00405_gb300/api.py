@@ -57,6 +57,16 @@ class Network:
                 "rt_network_set_enabled")
         return self
 
+    def set_rate_slopes(self, beta=None):
+        """Time-dependent rates c_k(t) = c_k (1 + beta_k t), beta_k >= 0 (Sec. 6, Eq. 29); None
+        returns to constant rates."""
+        b = None if beta is None else np.ascontiguousarray(beta, dtype=np.float64)
+        if b is not None and b.shape != (self.M,):
+            raise ValueError("beta must have one entry per reaction")
+        L.check(self.lib.rt_network_set_rate_slopes(self.handle, None if b is None else b.ctypes.data_as(ctypes.c_void_p)),
+                "rt_network_set_rate_slopes")
+        return self
+
     def info(self):
         n, m, md = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         nz = ctypes.c_int64()

@@ -211,6 +211,10 @@ extern "C" int rt_batch_create(int32_t n_nets, const rt_network *const *nets, co
       delete b;
       return set_error(RT_ERR_INVALID_ARG, "network %d is NULL or on another device", i);
     }
+    if (g->dev.beta) {
+      delete b;
+      return set_error(RT_ERR_UNSUPPORTED, "network %d has time-dependent rates; batches take constant rates", i);
+    }
     off[i] = total;
     total += align256(g->arena_bytes);
     const int M = g->dev.M, N = g->dev.N;
@@ -270,6 +274,7 @@ extern "C" int rt_batch_create(int32_t n_nets, const rt_network *const *nets, co
     memcpy(host.data() + off[i], g->host_blob.data(), g->arena_bytes);
     char *db = base + off[i];
     DevNet d = g->dev;  // same layout, rebased into the batch arena
+    d.beta = nullptr;
     d.rdesc = (const int2 *)(db + g->off_rdesc);
     d.c = (const double *)(db + g->off_c);
     d.c0 = (const double *)(db + g->off_c0);

@@ -692,8 +692,8 @@ extern "C" int rt_run_bundle_noalloc(const rt_network *net, const rt_run_params 
   int rc = validate_run(net, p, o);
   if (rc) return rc;
   if ((rc = check_device(net))) return rc;
-  if (p->form != RT_FORM_INTERNAL)
-    return set_error(RT_ERR_UNSUPPORTED, "rt_run_bundle_noalloc runs the internal-time form only");
+  if (p->form != RT_FORM_INTERNAL || net->dev.beta)
+    return set_error(RT_ERR_UNSUPPORTED, "rt_run_bundle_noalloc runs the internal-time form with constant rates only");
   RunArgs a;
   a.net = net->dev;
   a.x0 = p->x0_dev;

@@ -32,6 +32,7 @@ struct DevNet {
   const uint8_t *depw;     // [M][32] (M <= 256 only) bit r of depw[mu*32 + l]: channel l + 32 r depends on mu
   const uint8_t *depw16;   // [M][16] (M <= 128 only) the same for 16-lane segments: channel l + 16 r
   const uint8_t *depw8;    // [M][8]  (M <= 64 only)  the same for 8-lane segments: channel l + 8 r
+  const double *beta;      // [M] rate slopes, c_k(t) = c_k (1 + beta_k t); null for constant rates
   const int4 *vpack;       // [M] net change of reaction k packed in 16 bytes (null if it does not fit):
                            // up to 4 words (species << 8) | (delta & 0xFF), unused words 0
 };
@@ -64,6 +65,7 @@ struct rt_network {
   std::string host_blob;  // the arena's bytes
   size_t off_rdesc = 0, off_c = 0, off_c0 = 0, off_vptr = 0, off_vlist = 0, off_sptr = 0, off_slist = 0, off_dep = 0;
   std::vector<double> c_host;  // the network's rates (host copy)
+  double *beta_dev = nullptr;  // rate slopes on the device (rt_network_set_rate_slopes), or null
   size_t off_depw = 0, off_depw16 = 0, off_depw8 = 0;
   size_t off_vpack = 0;
   rt::SmallNet small = {};  // filled when M <= kSmallM and N <= kSmallN
@@ -105,6 +107,7 @@ int validate_run(const rt_network *net, const rt_run_params *p, const rt_outputs
 // Launchers implemented in the .cu files (return RT_OK or an error code).
 int launch_thread_mapping(const RunArgs &a, int block_threads, cudaStream_t s);
 int launch_rescaled_mapping(const RunArgs &a, int block_threads, cudaStream_t s);
+int launch_tdep_mapping(const RunArgs &a, int block_threads, cudaStream_t s);
 int launch_small_mapping(const RunArgs &a, const SmallNet &net, int block_threads, cudaStream_t s);
 int thread_mapping_max_m();
 size_t bundle_workspace_bytes(const DevNet &net, int64_t n_traj, int ctas_per_traj);

@@ -286,6 +286,7 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
 
 extern "C" void rt_network_destroy(rt_network *g) {
   if (!g) return;
+  if (g->beta_dev) cudaFree(g->beta_dev);
   if (g->arena) cudaFree(g->arena);
   delete g;
 }
@@ -317,5 +318,37 @@ extern "C" int rt_network_set_enabled(rt_network *g, const uint8_t *enabled) {
   memcpy(&g->host_blob[0] + g->off_c, eff.data(), sizeof(double) * M);
   if (g->small.ok)
     for (int32_t k = 0; k < M; k++) g->small.c[k] = eff[k];
+  return RT_OK;
+}
+
+extern "C" int rt_network_set_rate_slopes(rt_network *g, const double *beta) {
+  clear_error();
+  if (!g) return set_error(RT_ERR_INVALID_ARG, "rt_network_set_rate_slopes: NULL network");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != g->device) return set_error(RT_ERR_INVALID_ARG, "network lives on device %d, device %d is current", g->device, dev);
+  const int32_t M = g->dev.M;
+  if (!beta) {
+    if (g->beta_dev) cudaFree(g->beta_dev);
+    g->beta_dev = nullptr;
+    g->dev.beta = nullptr;
+    return RT_OK;
+  }
+  for (int32_t k = 0; k < M; k++)
+    if (!std::isfinite(beta[k]) || !(beta[k] >= 0.0))
+      return set_error(RT_ERR_INVALID_ARG, "rate slope beta[%d] = %g must be finite and >= 0", k, beta[k]);
+  std::vector<double> b(beta, beta + M);
+  for (auto &x : b)
+    if (x == 0.0) x = 0.0;  // -0.0 -> +0.0
+  if (!g->beta_dev) {
+    const cudaError_t e = cudaMalloc(&g->beta_dev, sizeof(double) * M);
+    if (e != cudaSuccess) {
+      g->beta_dev = nullptr;
+      return set_error(RT_ERR_OOM, "cudaMalloc: %s", cudaGetErrorString(e));
+    }
+  }
+  const cudaError_t e = cudaMemcpy(g->beta_dev, b.data(), sizeof(double) * M, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return set_error(RT_ERR_CUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+  g->dev.beta = g->beta_dev;
   return RT_OK;
 }

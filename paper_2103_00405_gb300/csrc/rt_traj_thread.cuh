@@ -437,4 +437,202 @@ __device__ __forceinline__ void simulate_rescaled(const RunArgs &A, const Thread
   if (A.out.t_last_dev) A.out.t_last_dev[j] = t;
 }
 
+// ---------------------------------------------------------------------------------
+// Time-dependent rates c_k(t) = c_k (1 + beta_k t) (Sec. 6, Eq. 29): with A_k = c_k h_k(X)
+// constant between events, channel k's internal time over [t, t + d] grows by
+// A_k I_k(t, d), I_k = d (1 + beta_k t) + beta_k d^2 / 2, and its waiting time solves
+// A_k I_k(t, d) = P_k - T_k, written without cancellation.  beta_k = 0 runs exactly the
+// constant-rate operations.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ double tdep_wait(double A, double beta, double R, double t) {
+  if (!(dbits(R) > 0)) return 0.0;
+  if (beta == 0.0) return __ddiv_rn(R, A);
+  const double u = __dadd_rn(1.0, __dmul_rn(beta, t));
+  const double b = __dmul_rn(A, u);
+  const double e = __dmul_rn(__dmul_rn(__dmul_rn(2.0, A), beta), R);
+  const double den = __dadd_rn(b, __dsqrt_rn(__dadd_rn(__dmul_rn(b, b), e)));
+  return __ddiv_rn(__dmul_rn(2.0, R), den);
+}
+
+__device__ __forceinline__ double tdep_integral(double beta, double t, double d) {
+  if (beta == 0.0) return d;
+  const double u = __dadd_rn(1.0, __dmul_rn(beta, t));
+  return __dadd_rn(__dmul_rn(d, u), __dmul_rn(__dmul_rn(__dmul_rn(beta, d), d), 0.5));
+}
+
+template <int MAXM, bool LL>
+__device__ __forceinline__ void simulate_tdep(const RunArgs &A, const ThreadNet &S, const double *beta, const int64_t j,
+                                              const int B, const int tend_finite, const int smem_mom) {
+  const int M = A.net.M, N = A.net.N;
+  int *X = S.X + threadIdx.x;  // X[s] lives at X[s * B]
+  auto xat = [&](int s) { return X[s * B]; };
+  const uint64_t g = (uint64_t)(A.traj_offset + j);
+  const int32_t *x0 = A.x0 + (A.per_traj_x0 ? j * (int64_t)N : 0);
+  bool bad = false;
+  for (int s = 0; s < N; ++s) {
+    const int v = x0[s];
+    X[s * B] = v;
+    bad |= v < 0;
+  }
+  double P[MAXM], T[MAXM], a[MAXM], bt[MAXM];
+  int32_t n[MAXM];
+  int status = RT_TRAJ_TEND;
+  double t = 0.0, ll = 0.0;
+  int32_t ev = 0;
+  int64_t gi = 0;
+  double next_g = 0.0;
+  auto record = [&](int64_t gidx) {
+    if (A.out.grid_dev) {
+      int32_t *gp = A.out.grid_dev + (j * A.G + gidx) * N;
+      for (int s = 0; s < N; ++s) gp[s] = X[s * B];
+    }
+    if (smem_mom) {
+      mom_add(S.mt, gidx, N, xat);
+    } else if (A.out.grid_sum_dev) {
+      for (int s = 0; s < N; ++s) {
+        const long long x = X[s * B];
+        atomicAdd((unsigned long long *)(A.out.grid_sum_dev + gidx * N + s), (unsigned long long)x);
+        if (A.out.grid_sumsq_dev)
+          atomicAdd((unsigned long long *)(A.out.grid_sumsq_dev + gidx * N + s), (unsigned long long)(x * x));
+      }
+      if (A.out.grid_count_dev) atomicAdd((unsigned long long *)(A.out.grid_count_dev + gidx), 1ull);
+    }
+  };
+#pragma unroll
+  for (int k = 0; k < MAXM; ++k) {
+    n[k] = 0;
+    T[k] = 0.0;
+    P[k] = 0.0;
+    a[k] = 0.0;
+    bt[k] = k < M ? beta[k] : 0.0;
+  }
+  if (bad) {
+    status = RT_TRAJ_BAD_X0;
+  } else {
+#pragma unroll
+    for (int k = 0; k < MAXM; ++k)
+      if (k < M) {
+        P[k] = exp1_draw(A.seed, g, (uint32_t)k, 0u, A.stream_id);
+        a[k] = propensity(S.rd[k], S.c[k], xat);
+      }
+    const int64_t tend_bits = dbits(A.t_end);
+    for (;;) {
+      // every channel's waiting time from its own integral (Eq. 29); smallest index on ties
+      int64_t best = kInfBits;
+      int mu = -1;
+#pragma unroll
+      for (int k = 0; k < MAXM; ++k)
+        if (k < M && dbits(a[k]) != 0) {
+          const int64_t wb = dbits(tdep_wait(a[k], bt[k], __dsub_rn(P[k], T[k]), t));
+          if (wb < best) {
+            best = wb;
+            mu = k;
+          }
+        }
+      if (mu < 0) {
+        status = RT_TRAJ_ABSORBED;
+        break;
+      }
+      const double dmin = bitsd(best);
+      const double tn = __dadd_rn(t, dmin);
+      if (dbits(tn) > tend_bits) {
+        status = RT_TRAJ_TEND;
+        break;
+      }
+      if (ev == A.max_events) {
+        status = RT_TRAJ_MAX_EVENTS;
+        break;
+      }
+      const int vb = S.vp[mu], ve = S.vp[mu + 1];
+      bool over = false;
+      for (int i = vb; i < ve; ++i) {
+        const int2 e = S.vl[i];
+        const long long nx = (long long)X[e.x * B] + e.y;
+        over |= (nx > INT_MAX) | (nx < 0);
+      }
+      if (over) {
+        status = RT_TRAJ_OVERFLOW;
+        break;
+      }
+      while (gi < A.G && dbits(next_g) < dbits(tn)) {
+        record(gi);
+        ++gi;
+        next_g = __dmul_rn(__ll2double_rn(gi), A.sample_dt);
+      }
+      const double tprev = t;
+      t = tn;
+      trace_event(A.out, j, ev, mu, tn);
+      double a_mu = 0.0, b_mu = 0.0;
+#pragma unroll
+      for (int k = 0; k < MAXM; ++k)
+        if (k < M) {
+          if (k == mu) {
+            a_mu = a[k];
+            b_mu = bt[k];
+          }
+          T[k] = __dadd_rn(T[k], __dmul_rn(a[k], tdep_integral(bt[k], tprev, dmin)));
+        }
+      if (LL) ll = __dadd_rn(ll, rt_ln(__dmul_rn(a_mu, __dadd_rn(1.0, __dmul_rn(b_mu, t)))));
+      for (int i = vb; i < ve; ++i) {
+        const int2 e = S.vl[i];
+        X[e.x * B] += e.y;
+      }
+      int32_t nmu = 0;
+#pragma unroll
+      for (int k = 0; k < MAXM; ++k)
+        if (k == mu) {
+          n[k] += 1;
+          nmu = n[k];
+        }
+      ++ev;
+      const double E = exp1_draw(A.seed, g, (uint32_t)mu, (uint32_t)nmu, A.stream_id);
+      const uint64_t dm = S.dep[mu];
+#pragma unroll
+      for (int k = 0; k < MAXM; ++k)
+        if (k < M) {
+          if (k == mu) P[k] = __dadd_rn(P[k], E);
+          if ((dm >> k) & 1ull) a[k] = propensity(S.rd[k], S.c[k], xat);
+        }
+    }
+  }
+  const bool known = status == RT_TRAJ_TEND || status == RT_TRAJ_ABSORBED;
+  for (; gi < A.G; ++gi) {
+    if (known) {
+      record(gi);
+    } else if (A.out.grid_dev) {
+      int32_t *gp = A.out.grid_dev + (j * A.G + gi) * N;
+      for (int s = 0; s < N; ++s) gp[s] = -1;
+    }
+  }
+  if (A.out.loglik_dev || A.out.t_internal_dev) {
+    if (known && tend_finite && status != RT_TRAJ_BAD_X0) {
+      const double rest = __dsub_rn(A.t_end, t);
+#pragma unroll
+      for (int k = 0; k < MAXM; ++k)
+        if (k < M) T[k] = __dadd_rn(T[k], __dmul_rn(a[k], tdep_integral(bt[k], t, rest)));
+    }
+    if (A.out.t_internal_dev)
+#pragma unroll
+      for (int k = 0; k < MAXM; ++k)
+        if (k < M) A.out.t_internal_dev[j * M + k] = T[k];
+    if (A.out.loglik_dev) {
+      double sT = 0.0;
+#pragma unroll
+      for (int k = 0; k < MAXM; ++k)
+        if (k < M) sT = __dadd_rn(sT, T[k]);
+      A.out.loglik_dev[j] = status == RT_TRAJ_BAD_X0 ? __longlong_as_double(0x7FF8000000000000ll) : __dsub_rn(ll, sT);
+    }
+  }
+  if (A.out.counts_dev)
+#pragma unroll
+    for (int k = 0; k < MAXM; ++k)
+      if (k < M) A.out.counts_dev[j * M + k] = n[k];
+  if (A.out.x_final_dev)
+    for (int s = 0; s < N; ++s) A.out.x_final_dev[j * N + s] = X[s * B];
+  trace_tail(A.out, j, ev, 0, 1);
+  if (A.out.n_events_dev) A.out.n_events_dev[j] = ev;
+  if (A.out.status_dev) A.out.status_dev[j] = status;
+  if (A.out.t_last_dev) A.out.t_last_dev[j] = t;
+}
+
 }  // namespace rt
