@@ -286,7 +286,7 @@ extern "C" int rt_batch_create(int32_t n_nets, const rt_network *const *nets, co
     d.depw = g->dev.depw ? (const uint8_t *)(db + g->off_depw) : nullptr;
     d.depw16 = g->dev.depw16 ? (const uint8_t *)(db + g->off_depw16) : nullptr;
     d.depw8 = g->dev.depw8 ? (const uint8_t *)(db + g->off_depw8) : nullptr;
-    d.vpack = g->dev.vpack ? (const int4 *)(db + g->off_vpack) : nullptr;
+    d.vdep = g->dev.vdep ? (const int4 *)(db + g->off_vdep) : nullptr;
     hn[i].d = d;
   }
   memcpy(host.data() + off_nets, hn.data(), sizeof(BNet) * n_nets);

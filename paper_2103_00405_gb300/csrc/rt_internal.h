@@ -33,8 +33,9 @@ struct DevNet {
   const uint8_t *depw16;   // [M][16] (M <= 128 only) the same for 16-lane segments: channel l + 16 r
   const uint8_t *depw8;    // [M][8]  (M <= 64 only)  the same for 8-lane segments: channel l + 8 r
   const double *beta;      // [M] rate slopes, c_k(t) = c_k (1 + beta_k t); null for constant rates
-  const int4 *vpack;       // [M] net change of reaction k packed in 16 bytes (null if it does not fit):
-                           // up to 4 words (species << 8) | (delta & 0xFF), unused words 0
+  const int4 *vdep;        // [M][3] per reaction, when it fits (else null): its net change packed in
+                           // 4 words (species << 8) | (delta & 0xFF), unused words 0; then for each
+                           // changed species the begin and the length of its reader list in slist
 };
 
 // Packed net-change word: species in the high 24 bits, delta (-128..127, never 0) in the low 8.
@@ -67,7 +68,7 @@ struct rt_network {
   std::vector<double> c_host;  // the network's rates (host copy)
   double *beta_dev = nullptr;  // rate slopes on the device (rt_network_set_rate_slopes), or null
   size_t off_depw = 0, off_depw16 = 0, off_depw8 = 0;
-  size_t off_vpack = 0;
+  size_t off_vdep = 0;
   rt::SmallNet small = {};  // filled when M <= kSmallM and N <= kSmallN
 };
 

@@ -21,7 +21,8 @@
 //      takes the same decision from the same C entries,
 //   3. fires: updates its own copy of X, draws the new increment if it owns mu,
 //   4. updates the touched channels of its slice (from the species -> readers lists),
-//   5. re-reduces the 32-channel groups that hold a touched channel (one warp each).
+//   5. updates the minima of the 32-channel groups that hold a touched channel (one thread per
+//      group; a group whose minimum was touched re-reads its untouched channels, one warp each).
 // Ties go to the smallest index at every level, so the minimum is the exact one.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
@@ -50,11 +51,14 @@ struct __align__(32) ChanRec {
   double a;  // propensity since s
 };
 
+constexpr int kPostWarp = kLazyWarps - 1;         // the root, its prefetch and the posts (no global stores)
+constexpr int kDrawTid = (kLazyWarps - 2) * 32;    // lane 0 of warp 14 updates the fired channel
+
 // a mailbox slot: the posting CTA's slice minimum for one event
 struct __align__(16) Mail {
   unsigned long long w;     // bits of tau (+inf if none)
   unsigned long long a;     // bits of its propensity
-  int4 v;                   // its packed net change (DevNet::vpack; zeros if not packed)
+  int4 v, rb, rl;           // its dependency record (DevNet::vdep; zeros if none)
   unsigned long long flag;  // (seq << 32) | (uint32)k, written last with release semantics
   unsigned long long pad;
 };
@@ -118,13 +122,18 @@ __device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank) {
   return out;
 }
 
-__device__ __forceinline__ void post_mail(uint32_t remote, unsigned long long w, unsigned long long a, int4 v,
-                                          unsigned long long flag) {
-  asm volatile("st.shared::cluster.v2.u64 [%0], {%1, %2};" ::"r"(remote), "l"(w), "l"(a) : "memory");
-  asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(remote + 16), "r"(v.x), "r"(v.y), "r"(v.z),
-               "r"(v.w)
+__device__ __forceinline__ void st_cluster_v4(uint32_t addr, int4 v) {
+  asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
                : "memory");
-  asm volatile("st.release.cluster.shared::cluster.u64 [%0], %1;" ::"r"(remote + 32), "l"(flag) : "memory");
+}
+
+__device__ __forceinline__ void post_mail(uint32_t remote, unsigned long long w, unsigned long long a, int4 v, int4 rb,
+                                          int4 rl, unsigned long long flag) {
+  asm volatile("st.shared::cluster.v2.u64 [%0], {%1, %2};" ::"r"(remote), "l"(w), "l"(a) : "memory");
+  st_cluster_v4(remote + 16, v);
+  st_cluster_v4(remote + 32, rb);
+  st_cluster_v4(remote + 48, rl);
+  asm volatile("st.release.cluster.shared::cluster.u64 [%0], %1;" ::"r"(remote + 64), "l"(flag) : "memory");
 }
 
 __device__ __forceinline__ unsigned long long acquire_flag(uint32_t cluster_addr) {
@@ -137,6 +146,19 @@ __device__ __forceinline__ bool lex_less(long long w1, int k1, long long w2, int
   return w1 < w2 || (w1 == w2 && k1 < k2);
 }
 
+// (w, k) lexicographic minimum over the 32 lanes of a warp
+__device__ __forceinline__ void warp_lexmin(long long &w, int &k) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long w2 = __shfl_xor_sync(0xFFFFFFFFu, w, o);
+    const int k2 = __shfl_xor_sync(0xFFFFFFFFu, k, o);
+    if (lex_less(w2, k2, w, k)) {
+      w = w2;
+      k = k2;
+    }
+  }
+}
+
 struct LazyDecision {
   int mu;       // fired channel (-1: none can fire)
   int stop;     // 0 continue, else 1 + status
@@ -147,16 +169,21 @@ struct LazyDecision {
   int2 vl[kLazyMaxVlen];
 };
 
+// a warp's candidate for the slice minimum with its prefetched dependency record
+struct PostStage {
+  long long w;
+  double a;
+  int4 v, rb, rl;
+  int k;
+};
+
 template <bool LL>
 __global__ void __launch_bounds__(kLazyThreads, 1) k_lazy(const LazyArgs L) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Mail mbox[2][kLazyMaxC];
-  __shared__ long long red_w[kLazyWarps];
-  __shared__ int red_k[kLazyWarps];
-  __shared__ double red_a[kLazyWarps];
-  __shared__ int4 red_v[kLazyWarps];
+  __shared__ PostStage red[kLazyWarps];  // each warp's candidate for the slice minimum
   __shared__ LazyDecision dec;
-  __shared__ int s_bad, s_ndirty, s_ntouch;
+  __shared__ int s_bad, s_ntouch, s_nrel, s_ngl;
   __shared__ int s_lofs[kLazyMaxVlen + 1];  // prefix offsets into the changed species' reader lists
   __shared__ int s_lbeg[kLazyMaxVlen];
 
@@ -169,26 +196,26 @@ __global__ void __launch_bounds__(kLazyThreads, 1) k_lazy(const LazyArgs L) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t k0 = (int64_t)c * L.chunk;
   const int64_t k1 = min((int64_t)M, k0 + L.chunk);
-  const int ng = (int)(L.chunk / 32);  // groups of this slice (the last CTA's may be past M)
+  const int ng = (int)(L.chunk / 32);  // 32-channel groups of this slice (the last CTA's may run past M)
   const int cap = L.cap;
 
-  // shared memory: per group its minimum (tau bits, channel) and its slot in this event's
-  // lists; X; species offsets; per slot (a group touched this event): the group, the minimum
-  // of its touched channels, whether its previous minimum was touched, which channels were
-  // touched; the touched channels and their new firing times
+  // shared memory: per group its minimum (tau bits, channel) and the head of this event's list
+  // of its touched channels; the touched channels of an event with their new firing times and
+  // list links; the touched groups; per reloaded group its touched-channel minimum and mask; X;
+  // species offsets
   long long *gw = (long long *)smem;
-  long long *scw = gw + ng;
-  long long *tw = scw + cap;
-  int *gk = (int *)(tw + cap);
-  int *gslot = gk + ng;
-  int *Xs = gslot + ng;
+  long long *tw = gw + ng;
+  long long *rcw = tw + cap;
+  int *gk = (int *)(rcw + cap);
+  int *ghead = gk + ng;
+  int *tk = ghead + ng;
+  int *tnext = tk + cap;
+  int *glist = tnext + cap;
+  int *rq = glist + cap;
+  int *rck = rq + cap;
+  uint32_t *rmask = (uint32_t *)(rck + cap);
+  int *Xs = (int *)(rmask + cap);
   int *sp = Xs + N;
-  uint32_t *dbm = (uint32_t *)(sp + (L.sptr_smem ? N + 1 : 0));
-  int *dlist = (int *)(dbm + (ng + 31) / 32);
-  int *sck = dlist + cap;
-  int *srl = sck + cap;
-  uint32_t *stbm = (uint32_t *)(srl + cap);
-  int *tk = (int *)(stbm + cap);
   const int *sptr = L.sptr_smem ? sp : r.net.sptr;
 
   ChanRec *CH = L.CH + j * L.Ms;
@@ -202,14 +229,15 @@ __global__ void __launch_bounds__(kLazyThreads, 1) k_lazy(const LazyArgs L) {
     Mail &m = mbox[i / kLazyMaxC][i % kLazyMaxC];
     m.w = 0;
     m.a = 0;
-    m.v = make_int4(0, 0, 0, 0);
+    m.v = m.rb = m.rl = make_int4(0, 0, 0, 0);
     m.flag = 0;
     m.pad = 0;
   }
   if (tid == 0) {
     s_bad = 0;
-    s_ndirty = 0;
     s_ntouch = 0;
+    s_nrel = 0;
+    s_ngl = 0;
   }
   __syncthreads();
   for (int s = tid; s < N; s += blockDim.x) {
@@ -219,13 +247,7 @@ __global__ void __launch_bounds__(kLazyThreads, 1) k_lazy(const LazyArgs L) {
   }
   if (L.sptr_smem)
     for (int s = tid; s <= N; s += blockDim.x) sp[s] = r.net.sptr[s];
-  for (int w = tid; w < (ng + 31) / 32; w += blockDim.x) dbm[w] = 0u;
-  for (int i = tid; i < cap; i += blockDim.x) {
-    scw[i] = kInfBits;
-    sck[i] = INT_MAX;
-    srl[i] = 0;
-    stbm[i] = 0u;
-  }
+  for (int q = tid; q < ng; q += blockDim.x) ghead[q] = -1;
   // group minima of the slice from the initial firing times
   for (int q = warp; q < ng; q += kLazyWarps) {
     const int64_t k = k0 + (int64_t)q * 32 + lane;
@@ -235,15 +257,7 @@ __global__ void __launch_bounds__(kLazyThreads, 1) k_lazy(const LazyArgs L) {
       w = dbits(TAU[k]);
       kk = (int)k;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const long long w2 = __shfl_xor_sync(0xFFFFFFFFu, w, o);
-      const int k2 = __shfl_xor_sync(0xFFFFFFFFu, kk, o);
-      if (lex_less(w2, k2, w, kk)) {
-        w = w2;
-        kk = k2;
-      }
-    }
+    warp_lexmin(w, kk);
     if (lane == 0) {
       gw[q] = w;
       gk[q] = kk;
@@ -261,8 +275,7 @@ __global__ void __launch_bounds__(kLazyThreads, 1) k_lazy(const LazyArgs L) {
   int64_t gi = 0;
   double next_g = 0.0;
   const int64_t tend_bits = dbits(r.t_end);
-  const int draw_tid = kLazyThreads - 32;  // lane 0 of the last warp updates the fired channel
-  int pend_k = -1;                         // draw thread: channel whose next increment is due
+  int pend_k = -1;  // draw thread: channel whose next increment is due
   int32_t pend_n = 0;
 
   auto record = [&](int64_t gidx, bool known) {  // CTA 0, all threads
@@ -280,64 +293,54 @@ __global__ void __launch_bounds__(kLazyThreads, 1) k_lazy(const LazyArgs L) {
       if (tid == 0 && r.out.grid_count_dev) atomicAdd((unsigned long long *)(r.out.grid_count_dev + gidx), 1ull);
     }
   };
-
-  // a touched channel k of the slice with new firing time bits w: its group gets a slot
-  // (once per event) and the channel joins the touched list
+  // a touched channel of the slice and its new firing time join this event's list and the
+  // list of its group; the first one of a group lists the group
   auto touch = [&](int64_t k, long long w) {
-    const int q = (int)((k - k0) >> 5);
-    const uint32_t bit = 1u << (q & 31);
-    if (!(atomicOr(&dbm[q >> 5], bit) & bit)) {
-      const int sl = atomicAdd(&s_ndirty, 1);
-      dlist[sl] = q;
-      gslot[q] = sl;
-    }
     const int i = atomicAdd(&s_ntouch, 1);
     tk[i] = (int)k;
     tw[i] = w;
+    const int q = (int)((k - k0) >> 5);
+    const int nx = atomicExch(&ghead[q], i);
+    tnext[i] = nx;
+    if (nx < 0) glist[atomicAdd(&s_ngl, 1)] = q;
   };
 
   if (!bad) {
     for (;;) {
-      // ---- 1. slice minimum over the group minima; each warp prefetches its candidate's
-      // packed net change and propensity while the block reduction completes
-      long long bw = kInfBits;
-      int bk = INT_MAX;
-      for (int q = tid; q < ng; q += blockDim.x) {
-        const long long w = gw[q];
-        const int kk = gk[q];
-        if (lex_less(w, kk, bw, bk)) {
-          bw = w;
-          bk = kk;
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const long long w2 = __shfl_xor_sync(0xFFFFFFFFu, bw, o);
-        const int k2 = __shfl_xor_sync(0xFFFFFFFFu, bk, o);
-        if (lex_less(w2, k2, bw, bk)) {
-          bw = w2;
-          bk = k2;
-        }
-      }
-      if (lane == 0) {
-        int4 v = make_int4(0, 0, 0, 0);
-        double av = 0.0;
-        if (bw != kInfBits) {
-          if (r.net.vpack) v = r.net.vpack[bk];
-          av = CH[bk].a;
-        }
-        red_w[warp] = bw;
-        red_k[warp] = bk;
-        red_v[warp] = v;
-        red_a[warp] = av;
-      }
-      __syncthreads();
-      // ---- 2. post it to every CTA of the cluster; collect the C posts of this event
+      // ---- 1. the slice minimum over the group minima; each warp prefetches its candidate's
+      // dependency record and propensity while the block reduction completes; a warp that never
+      // stores to global memory takes the final minimum and posts it to every CTA of the cluster
       seq += 1;
       const int par = seq & 1;
-      if (warp == 0) {
-        long long w = lane < kLazyWarps ? red_w[lane] : kInfBits;
-        int kk = lane < kLazyWarps ? red_k[lane] : INT_MAX;
+      {
+        long long w = kInfBits;
+        int kk = INT_MAX;
+        for (int q = tid; q < ng; q += blockDim.x)
+          if (lex_less(gw[q], gk[q], w, kk)) {
+            w = gw[q];
+            kk = gk[q];
+          }
+        warp_lexmin(w, kk);
+        if (lane == 0) {
+          PostStage &st = red[warp];
+          st.w = w;
+          st.k = kk;
+          st.v = st.rb = st.rl = make_int4(0, 0, 0, 0);
+          st.a = 0.0;
+          if (w != kInfBits) {
+            if (r.net.vdep) {
+              st.v = r.net.vdep[3 * (int64_t)kk];
+              st.rb = r.net.vdep[3 * (int64_t)kk + 1];
+              st.rl = r.net.vdep[3 * (int64_t)kk + 2];
+            }
+            st.a = CH[kk].a;
+          }
+        }
+      }
+      __syncthreads();
+      if (warp == kPostWarp) {
+        long long w = lane < kLazyWarps ? red[lane].w : kInfBits;
+        int kk = lane < kLazyWarps ? red[lane].k : INT_MAX;
         int src = lane;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -351,13 +354,14 @@ __global__ void __launch_bounds__(kLazyThreads, 1) k_lazy(const LazyArgs L) {
           }
         }
         if (lane < C) {
-          const int si = src < kLazyWarps ? src : 0;
+          const PostStage &st = red[src < kLazyWarps ? src : 0];
           const unsigned long long flag = ((unsigned long long)seq << 32) | (uint32_t)kk;
           const uint32_t slot = mb_local + (uint32_t)((par * kLazyMaxC + c) * sizeof(Mail));
-          post_mail(map_rank(slot, lane), (unsigned long long)w, (unsigned long long)dbits(red_a[si]), red_v[si], flag);
+          post_mail(map_rank(slot, lane), (unsigned long long)w, (unsigned long long)dbits(st.a), st.v, st.rb, st.rl,
+                    flag);
         }
       }
-      if (tid == draw_tid && pend_k >= 0) {
+      if (tid == kDrawTid && pend_k >= 0) {
         // the next increment of the channel this CTA fired last (Eq. 24, 27), drawn while the
         // cluster's posts arrive
         ENX[pend_k] = exp1_draw(r.seed, g, (uint32_t)pend_k, (uint32_t)(pend_n + 1), r.stream_id);
@@ -372,7 +376,7 @@ __global__ void __launch_bounds__(kLazyThreads, 1) k_lazy(const LazyArgs L) {
         int qbest = 0;
         const uint32_t own = map_rank(mb_local, (uint32_t)c);
         for (int q = 0; q < C && ok; ++q) {
-          const uint32_t fa = own + (uint32_t)((par * kLazyMaxC + q) * sizeof(Mail)) + 32;
+          const uint32_t fa = own + (uint32_t)((par * kLazyMaxC + q) * sizeof(Mail)) + 64;
           unsigned long long f = acquire_flag(fa);
           while ((unsigned int)(f >> 32) != seq) {
             if (++it > L.spin_limit) {
@@ -403,16 +407,33 @@ __global__ void __launch_bounds__(kLazyThreads, 1) k_lazy(const LazyArgs L) {
           dec.stop = 1 + RT_TRAJ_MAX_EVENTS;
         } else {
           int vlen = 0;
-          if (r.net.vpack) {
-            const int4 v = mbox[par][qbest].v;
-            const int vw[4] = {v.x, v.y, v.z, v.w};
+          int tot = 0;
+          if (r.net.vdep) {
+            const Mail &m = mbox[par][qbest];
+            const int vw[4] = {m.v.x, m.v.y, m.v.z, m.v.w};
+            const int rb[4] = {m.rb.x, m.rb.y, m.rb.z, m.rb.w};
+            const int rl[4] = {m.rl.x, m.rl.y, m.rl.z, m.rl.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-              if (vpack_delta(vw[i]) != 0) dec.vl[vlen++] = make_int2(vpack_species(vw[i]), vpack_delta(vw[i]));
+              if (vpack_delta(vw[i]) != 0) {
+                dec.vl[vlen] = make_int2(vpack_species(vw[i]), vpack_delta(vw[i]));
+                s_lbeg[vlen] = rb[i];
+                s_lofs[vlen] = tot;
+                tot += rl[i];
+                ++vlen;
+              }
           } else {
             const int vb = r.net.vptr[kk], ve = r.net.vptr[kk + 1];
-            for (int i = vb; i < ve; ++i) dec.vl[vlen++] = r.net.vlist[i];
+            for (int i = vb; i < ve; ++i) {
+              const int2 e = r.net.vlist[i];
+              dec.vl[vlen] = e;
+              s_lbeg[vlen] = sptr[e.x];
+              s_lofs[vlen] = tot;
+              tot += sptr[e.x + 1] - sptr[e.x];
+              ++vlen;
+            }
           }
+          s_lofs[vlen] = tot;
           bool over = false;
           for (int i = 0; i < vlen; ++i) {
             const long long nx = (long long)Xs[dec.vl[i].x] + dec.vl[i].y;
@@ -426,15 +447,6 @@ __global__ void __launch_bounds__(kLazyThreads, 1) k_lazy(const LazyArgs L) {
             dec.tmin = bitsd(w);
             dec.a_mu = __longlong_as_double((long long)mbox[par][qbest].a);
             dec.grid = (c == 0 && gi < r.G && dbits(next_g) < w) ? 1 : 0;
-            // prefix offsets of the changed species' reader lists
-            int tot = 0;
-            for (int i = 0; i < vlen; ++i) {
-              const int s = dec.vl[i].x;
-              s_lbeg[i] = sptr[s];
-              s_lofs[i] = tot;
-              tot += sptr[s + 1] - sptr[s];
-            }
-            s_lofs[vlen] = tot;
           }
         }
       }
@@ -453,7 +465,7 @@ __global__ void __launch_bounds__(kLazyThreads, 1) k_lazy(const LazyArgs L) {
         }
         __syncthreads();  // X is read by the recording before it changes
       }
-      // ---- 3. fire: X += v_mu (Eq. 5), bookkeeping
+      // ---- 2. fire: X += v_mu (Eq. 5), bookkeeping
       t = tn;
       if (c == 0 && tid == 0) {
         trace_event(r.out, j, ev, mu, tn);
@@ -463,8 +475,8 @@ __global__ void __launch_bounds__(kLazyThreads, 1) k_lazy(const LazyArgs L) {
       const int vlen = dec.vlen;
       if (tid < vlen) Xs[dec.vl[tid].x] += dec.vl[tid].y;  // species are distinct within one reaction
       __syncthreads();
-      // ---- 4. the touched channels of this slice: new a_k and tau_k
-      if (tid == draw_tid && mu >= k0 && mu < k1) {
+      // ---- 3. the touched channels of this slice: new a_k and tau_k
+      if (tid == kDrawTid && mu >= k0 && mu < k1) {
         // the fired channel: internal time up to the event, its next increment (drawn ahead,
         // Eq. 27), new propensity and firing time
         ChanRec q = CH[mu];
@@ -481,9 +493,9 @@ __global__ void __launch_bounds__(kLazyThreads, 1) k_lazy(const LazyArgs L) {
         touch(mu, dbits(tau));
         pend_k = mu;
         pend_n = n;
-      } else if (tid < draw_tid) {
+      } else if (tid < kDrawTid) {
         const int tot = s_lofs[vlen];
-        for (int e = tid; e < tot; e += draw_tid) {
+        for (int e = tid; e < tot; e += kDrawTid) {
           int li = 0;
           while (e >= s_lofs[li + 1]) ++li;
           const int64_t k = r.net.slist[s_lbeg[li] + (e - s_lofs[li])];
@@ -507,67 +519,67 @@ __global__ void __launch_bounds__(kLazyThreads, 1) k_lazy(const LazyArgs L) {
         }
       }
       __syncthreads();
-      // ---- 5. group minima.  A group whose previous minimum was not touched takes the smaller
-      // of that minimum and its touched channels' minimum; a group whose minimum was touched is
-      // re-reduced (its untouched channels from memory).
-      const int nt = s_ntouch;
-      for (int i = tid; i < nt; i += blockDim.x) {
-        const int k = tk[i];
-        const int q = (k - (int)k0) >> 5;
-        const int sl = gslot[q];
-        atomicOr(&stbm[sl], 1u << (k & 31));  // slices start at multiples of 32
-        if (gk[q] == k) srl[sl] = 1;
-        atomicMin(&scw[sl], tw[i]);
+      // ---- 4. group minima, one thread per touched group.  A group whose previous minimum was not
+      // touched takes the smaller of that minimum and its touched channels' minimum; a group whose
+      // minimum was touched is reloaded below (its untouched channels from memory).
+      const int ngl = s_ngl;
+      for (int gi2 = tid; gi2 < ngl; gi2 += blockDim.x) {
+        const int q = glist[gi2];
+        long long bw = kInfBits;
+        int bk = INT_MAX;
+        uint32_t bits = 0;
+        bool hit = false;
+        const int old_k = gk[q];
+        for (int i = ghead[q]; i >= 0; i = tnext[i]) {
+          const int k = tk[i];
+          const long long w = tw[i];
+          bits |= 1u << (k & 31);  // slices start at multiples of 32
+          hit |= k == old_k;
+          if (lex_less(w, k, bw, bk)) {
+            bw = w;
+            bk = k;
+          }
+        }
+        ghead[q] = -1;
+        if (hit) {
+          const int ri = atomicAdd(&s_nrel, 1);
+          rq[ri] = q;
+          rcw[ri] = bw;
+          rck[ri] = bk;
+          rmask[ri] = bits;
+        } else {
+          if (lex_less(bw, bk, gw[q], gk[q])) {
+            gw[q] = bw;
+            gk[q] = bk;
+          }
+        }
       }
       __syncthreads();
-      for (int i = tid; i < nt; i += blockDim.x) {
-        const int k = tk[i];
-        const int sl = gslot[(k - (int)k0) >> 5];
-        if (tw[i] == scw[sl]) atomicMin(&sck[sl], k);
-      }
-      __syncthreads();
-      const int nd = s_ndirty;
-      for (int sl = warp; sl < nd; sl += kLazyWarps) {
-        const int q = dlist[sl];
+      const int nrel = s_nrel;
+      for (int ri = warp; ri < nrel; ri += kLazyWarps) {
+        const int q = rq[ri];
+        const int64_t k = k0 + (int64_t)q * 32 + lane;
         long long w = kInfBits;
         int kk = INT_MAX;
-        if (srl[sl]) {
-          const int64_t k = k0 + (int64_t)q * 32 + lane;
-          if (k < k1 && !((stbm[sl] >> lane) & 1u)) {
-            w = dbits(__ldcg(TAU + k));
-            kk = (int)k;
-          }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            const long long w2 = __shfl_xor_sync(0xFFFFFFFFu, w, o);
-            const int k2 = __shfl_xor_sync(0xFFFFFFFFu, kk, o);
-            if (lex_less(w2, k2, w, kk)) {
-              w = w2;
-              kk = k2;
-            }
-          }
-        } else {
-          w = gw[q];
-          kk = gk[q];
+        if (k < k1 && !((rmask[ri] >> lane) & 1u)) {
+          w = dbits(__ldcg(TAU + k));
+          kk = (int)k;
         }
+        warp_lexmin(w, kk);
         if (lane == 0) {
-          if (lex_less(scw[sl], sck[sl], w, kk)) {
-            w = scw[sl];
-            kk = sck[sl];
+          if (lex_less(rcw[ri], rck[ri], w, kk)) {
+            w = rcw[ri];
+            kk = rck[ri];
           }
           gw[q] = w;
           gk[q] = kk;
-          dbm[q >> 5] = 0u;
-          scw[sl] = kInfBits;
-          sck[sl] = INT_MAX;
-          srl[sl] = 0;
-          stbm[sl] = 0u;
         }
       }
       __syncthreads();
       if (tid == 0) {
-        s_ndirty = 0;
         s_ntouch = 0;
+        s_nrel = 0;
+        s_ngl = 0;
       }
     }
   }
@@ -641,8 +653,8 @@ static LazyPlan plan_lazy(const DevNet &net, int max_dependents, int64_t n_traj,
   // touched channels of one event in one slice: at most the fired channel and the readers of
   // the species it changes (max_dependents counts them with multiplicity)
   p.cap = (int)std::min<int64_t>(p.chunk, (int64_t)max_dependents + 1);
-  const size_t base = (size_t)ng * 16 + (size_t)p.cap * (8 + 8 + 4 + 4 + 4 + 4 + 4) + (size_t)net.N * 4 +
-                      (size_t)((ng + 31) / 32) * 4;
+  // gw, gk, ghead per group; tw, rcw, tk, tnext, glist, rq, rck, rmask per touched channel; X
+  const size_t base = (size_t)ng * (8 + 4 + 4) + (size_t)p.cap * (8 + 8 + 4 + 4 + 4 + 4 + 4 + 4) + (size_t)net.N * 4;
   p.sptr_smem = base + (size_t)(net.N + 1) * 4 <= smem_budget ? 1 : 0;
   p.smem = base + (p.sptr_smem ? (size_t)(net.N + 1) * 4 : 0);
   return p;

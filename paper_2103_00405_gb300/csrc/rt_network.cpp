@@ -184,19 +184,26 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
   if (M <= 256) depw = dep_bytes(32);
   if (M <= 128) depw16 = dep_bytes(16);
   if (M <= 64) depw8 = dep_bytes(8);
-  // the net change of every reaction in 16 bytes, when every reaction changes at most 4
-  // species by -128..127 and N < 2^24 (one load per fired reaction in the tree mapping)
-  std::vector<int4> vpack;
+  // per reaction in 48 bytes, when every reaction changes at most 4 species by -128..127 and
+  // N < 2^24: its packed net change and the reader lists of the species it changes (one load
+  // per fired reaction in the tree mapping)
+  std::vector<int4> vdep;
   {
     bool fits = max_vlen <= 4 && N < (1 << 24);
     for (size_t i = 0; i < vlist.size() && fits; i++) fits = vlist[i].y >= -128 && vlist[i].y <= 127;
     if (fits) {
-      vpack.assign(M, make_int4(0, 0, 0, 0));
+      vdep.assign((size_t)3 * M, make_int4(0, 0, 0, 0));
       for (int32_t k = 0; k < M; k++) {
-        int w[4] = {0, 0, 0, 0};
-        for (int32_t i = vptr[k]; i < vptr[k + 1]; i++)
-          w[i - vptr[k]] = (int)(((unsigned)vlist[i].x << 8) | ((unsigned)vlist[i].y & 0xFFu));
-        vpack[k] = make_int4(w[0], w[1], w[2], w[3]);
+        int w[4] = {0, 0, 0, 0}, rb[4] = {0, 0, 0, 0}, rl[4] = {0, 0, 0, 0};
+        for (int32_t i = vptr[k]; i < vptr[k + 1]; i++) {
+          const int32_t sp = vlist[i].x, q = i - vptr[k];
+          w[q] = (int)(((unsigned)sp << 8) | ((unsigned)vlist[i].y & 0xFFu));
+          rb[q] = sptr[sp];
+          rl[q] = sptr[sp + 1] - sptr[sp];
+        }
+        vdep[(size_t)3 * k] = make_int4(w[0], w[1], w[2], w[3]);
+        vdep[(size_t)3 * k + 1] = make_int4(rb[0], rb[1], rb[2], rb[3]);
+        vdep[(size_t)3 * k + 2] = make_int4(rl[0], rl[1], rl[2], rl[3]);
       }
     }
   }
@@ -218,7 +225,7 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
   g->off_depw = off; off = align_up(off + std::max<size_t>(1, depw.size()), 256);
   g->off_depw16 = off; off = align_up(off + std::max<size_t>(1, depw16.size()), 256);
   g->off_depw8 = off; off = align_up(off + std::max<size_t>(1, depw8.size()), 256);
-  g->off_vpack = off; off = align_up(off + sizeof(int4) * std::max<size_t>(1, vpack.size()), 256);
+  g->off_vdep = off; off = align_up(off + sizeof(int4) * std::max<size_t>(1, vdep.size()), 256);
   g->arena_bytes = off;
   g->host_blob.assign(off, '\0');
   char *hb = &g->host_blob[0];
@@ -234,7 +241,7 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
   if (!depw.empty()) memcpy(hb + g->off_depw, depw.data(), depw.size());
   if (!depw16.empty()) memcpy(hb + g->off_depw16, depw16.data(), depw16.size());
   if (!depw8.empty()) memcpy(hb + g->off_depw8, depw8.data(), depw8.size());
-  if (!vpack.empty()) memcpy(hb + g->off_vpack, vpack.data(), sizeof(int4) * vpack.size());
+  if (!vdep.empty()) memcpy(hb + g->off_vdep, vdep.data(), sizeof(int4) * vdep.size());
 
   cudaGetDevice(&g->device);
   cudaError_t e = cudaMalloc(&g->arena, g->arena_bytes);
@@ -266,7 +273,7 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
   d.depw = M <= 256 ? (const uint8_t *)(db + g->off_depw) : nullptr;
   d.depw16 = M <= 128 ? (const uint8_t *)(db + g->off_depw16) : nullptr;
   d.depw8 = M <= 64 ? (const uint8_t *)(db + g->off_depw8) : nullptr;
-  d.vpack = vpack.empty() ? nullptr : (const int4 *)(db + g->off_vpack);
+  d.vdep = vdep.empty() ? nullptr : (const int4 *)(db + g->off_vdep);
   g->max_dependents = max_dep;
   g->n_dep_nz = dep_nz;
   if (M <= kSmallM && N <= kSmallN) {
