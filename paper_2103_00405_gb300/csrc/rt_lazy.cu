@@ -519,9 +519,11 @@ __global__ void __launch_bounds__(kLazyThreads, 1) k_lazy(const LazyArgs L) {
         }
       }
       __syncthreads();
-      // ---- 4. group minima, one thread per touched group.  A group whose previous minimum was not
-      // touched takes the smaller of that minimum and its touched channels' minimum; a group whose
-      // minimum was touched is reloaded below (its untouched channels from memory).
+      // ---- 4. group minima, one thread per touched group.  A group takes the smaller of its
+      // previous minimum and its touched channels' minimum, unless its previous minimum channel was
+      // touched and its tau grew: then every untouched channel may now be smaller, and the group is
+      // reloaded below (its untouched channels from memory).  (If that channel's tau did not grow,
+      // every untouched channel still lies above it.)
       const int ngl = s_ngl;
       for (int gi2 = tid; gi2 < ngl; gi2 += blockDim.x) {
         const int q = glist[gi2];
@@ -530,11 +532,12 @@ __global__ void __launch_bounds__(kLazyThreads, 1) k_lazy(const LazyArgs L) {
         uint32_t bits = 0;
         bool hit = false;
         const int old_k = gk[q];
+        const long long old_w = gw[q];
         for (int i = ghead[q]; i >= 0; i = tnext[i]) {
           const int k = tk[i];
           const long long w = tw[i];
           bits |= 1u << (k & 31);  // slices start at multiples of 32
-          hit |= k == old_k;
+          hit |= k == old_k && w > old_w;  // tau >= 0: bit patterns order like the values
           if (lex_less(w, k, bw, bk)) {
             bw = w;
             bk = k;
