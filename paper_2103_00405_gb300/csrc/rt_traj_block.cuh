@@ -9,9 +9,10 @@
 //      its internal times with the pre-event propensities (Eq. 17), recomputes the
 //      marked propensities (Eq. 1-2) and proposes its smallest certified upper
 //      bound of the waiting time;
-//   3. the block's best candidate is computed exactly and broadcast, every thread
-//      computes exactly only channels not certified to be larger, and a block
-//      reduction on (waiting time bits, channel) gives the exact argmin (Eq. 25-26).
+//   3. each warp's best candidate is computed exactly by its owner and published with
+//      the warp's bound; every thread takes the block's best candidate from those, computes
+//      exactly only channels not certified to be larger, and a block reduction on
+//      (waiting time bits, channel) gives the exact argmin (Eq. 25-26).
 #pragma once
 #include <climits>
 
@@ -37,6 +38,7 @@ struct BlockScratch {
   float *red_u;     // [warps]
   int *red_k;       // [warps]
   long long *red_w; // [warps]
+  long long *red_x; // [warps] exact waiting time (bits) of each warp's candidate
   int *red_k2;      // [warps]
   double *buf;      // [B] (and the broadcast slots below)
   long long *s_wc;  // candidate's exact waiting time
@@ -47,7 +49,7 @@ struct BlockScratch {
 
 __host__ __device__ inline size_t block_scratch_bytes(int M, int N, int B) {
   const int W = B / 32;
-  return (size_t)N * 4 + (size_t)M * 4 + (size_t)((M + 31) / 32) * 4 + (size_t)W * (4 + 4 + 8 + 4) +
+  return (size_t)N * 4 + (size_t)M * 4 + (size_t)((M + 31) / 32) * 4 + (size_t)W * (4 + 4 + 8 + 8 + 4) +
          (size_t)B * 8 + 32 + 64;
 }
 
@@ -56,7 +58,8 @@ __device__ inline BlockScratch carve_block_scratch(unsigned char *base, int M, i
   BlockScratch s;
   s.buf = (double *)base;
   s.red_w = (long long *)(s.buf + B);
-  s.s_wc = s.red_w + W;
+  s.red_x = s.red_w + W;
+  s.s_wc = s.red_x + W;
   s.s_amu = (double *)(s.s_wc + 1);
   s.s_E = s.s_amu + 1;
   s.red_u = (float *)(s.s_E + 1);
@@ -175,16 +178,26 @@ __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNe
           kub = k2;
         }
       }
-      if (lane == 0) {
+      // the warp candidate's owner computes its exact waiting time now, so the block's
+      // candidate is known exactly right after the reduction (one barrier, not two)
+      if (kub != INT_MAX && tid == kub % B) {
+        const int rs = kub / B;
+        S.red_x[warp] = dbits(waiting_time(pick<R>(P, rs), pick<R>(T, rs), pick<R>(a, rs)));
+        S.red_u[warp] = ub;
+        S.red_k[warp] = kub;
+      } else if (kub == INT_MAX && lane == 0) {
         S.red_u[warp] = ub;
         S.red_k[warp] = kub;
       }
       __syncthreads();
-      ub = S.red_u[0];
-      kub = S.red_k[0];
-      for (int w = 1; w < W; ++w) {
-        const float u2 = S.red_u[w];
-        const int k2 = S.red_k[w];
+      // every warp reduces the W warp minima itself (lane w reads warp w's): the block minimum
+      // in every thread without another barrier (lexicographic minimum: order-independent)
+      ub = lane < W ? S.red_u[lane] : __int_as_float(0x7F800000);
+      kub = lane < W ? S.red_k[lane] : INT_MAX;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float u2 = __shfl_xor_sync(0xFFFFFFFFu, ub, o);
+        const int k2 = __shfl_xor_sync(0xFFFFFFFFu, kub, o);
         if (u2 < ub || (u2 == ub && k2 < kub)) {
           ub = u2;
           kub = k2;
@@ -194,13 +207,9 @@ __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNe
         status = RT_TRAJ_ABSORBED;
         break;
       }
-      // ---- the best candidate exactly, then every channel not certified larger (Eq. 25-26)
-      if (tid == (kub % B)) {
-        const int rs = kub / B;
-        *S.s_wc = dbits(waiting_time(pick<R>(P, rs), pick<R>(T, rs), pick<R>(a, rs)));
-      }
-      __syncthreads();
-      const long long wc = *S.s_wc;
+      // ---- the best candidate exactly (from its warp's slot), then every channel not certified
+      // larger (Eq. 25-26)
+      const long long wc = S.red_x[(kub % B) >> 5];
       const float thr = f32_upper(bitsd(wc));
       long long bw = wc;
       int bk = kub;
@@ -229,11 +238,12 @@ __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNe
         S.red_k2[warp] = bk;
       }
       __syncthreads();
-      bw = S.red_w[0];
-      bk = S.red_k2[0];
-      for (int w = 1; w < W; ++w) {
-        const long long w2 = S.red_w[w];
-        const int k2 = S.red_k2[w];
+      bw = lane < W ? S.red_w[lane] : LLONG_MAX;
+      bk = lane < W ? S.red_k2[lane] : INT_MAX;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long w2 = __shfl_xor_sync(0xFFFFFFFFu, bw, o);
+        const int k2 = __shfl_xor_sync(0xFFFFFFFFu, bk, o);
         if (w2 < bw || (w2 == bw && k2 < bk)) {
           bw = w2;
           bk = k2;
