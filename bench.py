@@ -283,6 +283,35 @@ def cpu_baseline(cfgs, sample):
                       % (sample, cfgs[0]["t_end"], ev, dt)}
 
 
+def cpu_other_configs():
+    """The oracle on bounded samples of the other configurations: the ensemble on one core, the
+    large network (one trajectory, 200 events: each event recomputes and scans all 10^6 channels),
+    the gradient network with the likelihood (256 trajectories on every core)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    out = {}
+
+    def timed(name, desc, fn):
+        t0 = time.perf_counter()
+        ev = fn()
+        dt = time.perf_counter() - t0
+        out[name] = {"value": ev / dt, "unit": UNIT, "cores": desc[0], "sample": "%s (%d events, %.1f s)"
+                     % (desc[1], ev, dt)}
+
+    cfgs = W.ensemble_configs(32)
+    timed("ensemble_single_core", (1, "32 trajectories of each ensemble network to t_end=10, one thread"),
+          lambda: sum(int(oracle.run(c["net"], c["x0"], c["t_end"], 32, seed=c["seed"], max_events=c["max_events"],
+                                     n_threads=1)["n_events"].sum()) for c in cfgs))
+    big = W.large_network_config(max_events=200)
+    timed("large_network", (1, "1 trajectory x 200 events of the N=1e4, M=1e6 network, one thread"),
+          lambda: int(oracle.run(big["net"], big["x0"], big["t_end"], 1, seed=1, max_events=200)["n_events"].sum()))
+    gc = W.grad_config(256)
+    timed("gradient", (threads, "256 trajectories of the M=64 gradient network to t_end=5 with the likelihood"),
+          lambda: int(oracle.run(gc["net"], gc["x0"], gc["t_end"], 256, seed=1, want_grad=True,
+                                 n_threads=threads)["n_events"].sum()))
+    return out
+
+
 ENSEMBLE_WORKLOAD = ("ensemble: Lotka-Volterra (Table 4, X0=Y0=1000) + birth-death (k=100, gamma=1) "
                      "+ dimerisation (0.001/0.1, A0=1000), 2^20 trajectories each, t_end=10, "
                      "one thread per trajectory")
@@ -490,6 +519,7 @@ def run_ensemble(args, ctx):
     }
     if not args.no_cpu_baseline and ctx.world == 1:
         line["cpu_baseline"] = cpu_baseline(cfgs, args.cpu_sample)
+        line["cpu_baseline"]["other_configs"] = cpu_other_configs()
     return line
 
 
