@@ -136,6 +136,11 @@ __device__ __forceinline__ void post_mail(uint32_t remote, unsigned long long w,
   asm volatile("st.release.cluster.shared::cluster.u64 [%0], %1;" ::"r"(remote + 64), "l"(flag) : "memory");
 }
 
+// a hint: bring the line holding p into L2 (no register result, never faults on a valid address)
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ unsigned long long acquire_flag(uint32_t cluster_addr) {
   unsigned long long v;
   asm volatile("ld.acquire.cluster.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(cluster_addr) : "memory");
@@ -359,6 +364,29 @@ __global__ void __launch_bounds__(kLazyThreads, 1) k_lazy(const LazyArgs L) {
           const uint32_t slot = mb_local + (uint32_t)((par * kLazyMaxC + c) * sizeof(Mail));
           post_mail(map_rank(slot, lane), (unsigned long long)w, (unsigned long long)dbits(st.a), st.v, st.rb, st.rl,
                     flag);
+        }
+        // While the posts travel: if this slice's candidate is the one that fires, the touched-
+        // channel phase of every CTA starts by reading its reader lists.  Prefetch their lines
+        // into L2 now (one CTA's candidate fires, so one CTA's prefetch is the useful one; the
+        // others cost L2 traffic only), with the fired channel's own record, increment and group.
+        if (w != kInfBits && r.net.vdep) {
+          const PostStage &st = red[src < kLazyWarps ? src : 0];
+          const int vw[4] = {st.v.x, st.v.y, st.v.z, st.v.w};
+          const int rb[4] = {st.rb.x, st.rb.y, st.rb.z, st.rb.w};
+          const int rl[4] = {st.rl.x, st.rl.y, st.rl.z, st.rl.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            if (vpack_delta(vw[i]) == 0 || rl[i] <= 0) continue;
+            const uintptr_t b = (uintptr_t)(r.net.slist + rb[i]) & ~(uintptr_t)127;
+            const uintptr_t e = (uintptr_t)(r.net.slist + rb[i] + rl[i] - 1);
+            for (uintptr_t a = b + (uintptr_t)lane * 128; a <= e; a += 32 * 128) prefetch_l2((const void *)a);
+          }
+          if (lane == 0) {
+            prefetch_l2(CH + kk);
+            prefetch_l2(ENX + kk);
+            prefetch_l2(TAU + (kk & ~31));
+            prefetch_l2(TAU + (kk & ~31) + 16);
+          }
         }
       }
       if (tid == kDrawTid && pend_k >= 0) {
