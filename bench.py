@@ -81,6 +81,7 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--t-end", type=float, default=10.0, help="ensemble horizon (reduced only for profiling captures)")
     ap.add_argument("--e2e-steps", type=int, default=3, help="ensemble: steps of the end-to-end leg (0: none)")
+    ap.add_argument("--skip-e2e", action="store_true", help="no end-to-end leg (the same as --e2e-steps 0)")
     ap.add_argument("--sub-steps", type=int, default=2, help="timed steps of each workload of the `workloads` object")
     ap.add_argument("--sub-warmup", type=int, default=1, help="warm-up steps of each workload of `workloads`")
     ap.add_argument("--batch-events", type=int, default=20_000, help="batched workload: event cap per network")
@@ -89,7 +90,10 @@ def parse(argv=None):
     ap.add_argument("--tree-events", type=int, default=1_000_000,
                     help="large_tree workload: events per trajectory per step (the configuration's 1e6)")
     ap.add_argument("--grad-traj", type=int, default=65536, help="grad workload: trajectories")
-    return ap.parse_args(argv)
+    args = ap.parse_args(argv)
+    if args.skip_e2e:
+        args.e2e_steps = 0
+    return args
 
 
 # ----------------------------------------------------------------------------------------
