@@ -190,8 +190,9 @@ int rt_network_set_enabled(rt_network *net, const uint8_t *enabled);
  * u = 1 + beta_k t, b = A_k u, R = P_k - T_k (for beta_k = 0: R / A_k, the constant-rate
  * operations); ln a_mu is taken at the event time.  The gradient (n_k - T_k) / c_k keeps
  * its form.  Networks with slopes run the internal-time form on the thread mapping
- * (M <= 16); other mappings and batches return RT_ERR_UNSUPPORTED.  Copies to the
- * device synchronously; no work using the network may be in flight.
+ * (M <= 16) or the warp mapping (M <= 256, 32 lanes per trajectory; the default above
+ * 16 reactions); other mappings, forms and batches return RT_ERR_UNSUPPORTED.  Copies to
+ * the device synchronously; no work using the network may be in flight.
  */
 int rt_network_set_rate_slopes(rt_network *net, const double *beta);
 

@@ -95,10 +95,13 @@ extern "C" int rt_run(const rt_network *net, const rt_run_params *p, const rt_ou
   if ((p->form == RT_FORM_ABSOLUTE) != (mapping == RT_MAP_TREE))
     return set_error(RT_ERR_UNSUPPORTED, "the absolute-time form runs on the tree mapping (RT_MAP_TREE) and the "
                      "tree mapping runs the absolute-time form only");
-  if (net->dev.beta) {  // time-dependent rates: the internal-time form on the thread mapping
-    if (p->form != RT_FORM_INTERNAL || mapping != RT_MAP_THREAD)
-      return set_error(RT_ERR_UNSUPPORTED, "time-dependent rates run the internal-time form on the thread mapping");
-    return launch_tdep_mapping(a, B, s);
+  if (net->dev.beta) {  // time-dependent rates: the internal-time form on the thread or warp mapping
+    if (p->form != RT_FORM_INTERNAL || (mapping != RT_MAP_THREAD && mapping != RT_MAP_WARP))
+      return set_error(RT_ERR_UNSUPPORTED,
+                       "time-dependent rates run the internal-time form on the thread (M <= 16) or warp (M <= 256) "
+                       "mapping");
+    return mapping == RT_MAP_THREAD ? launch_tdep_mapping(a, B, s)
+                                    : launch_tdep_warp_mapping(a, cfg ? cfg->lanes_per_traj : 0, s);
   }
   if (p->form == RT_FORM_RESCALED) {
     if (mapping != RT_MAP_THREAD) return set_error(RT_ERR_UNSUPPORTED, "Table 3's rescaled form runs on the thread mapping");

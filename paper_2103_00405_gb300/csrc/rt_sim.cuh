@@ -83,6 +83,26 @@ __device__ __forceinline__ double waiting_time(double P, double T, double a) {
   return dbits(rem) > 0 ? __ddiv_rn(rem, a) : 0.0;
 }
 
+// Time-dependent rates c_k(t) = c_k (1 + beta_k t) (Sec. 6, Eq. 29): with A = c_k h_k(X)
+// constant between events, the waiting time d solving A (d (1 + beta t) + beta d^2 / 2) = R
+// for the remaining internal time R = P - T (the positive root, written without cancellation),
+// and the integral of 1 + beta s over [t, t + d].  beta = 0 gives the constant-rate operations.
+__device__ __forceinline__ double tdep_wait(double A, double beta, double R, double t) {
+  if (!(dbits(R) > 0)) return 0.0;
+  if (beta == 0.0) return __ddiv_rn(R, A);
+  const double u = __dadd_rn(1.0, __dmul_rn(beta, t));
+  const double b = __dmul_rn(A, u);
+  const double e = __dmul_rn(__dmul_rn(__dmul_rn(2.0, A), beta), R);
+  const double den = __dadd_rn(b, __dsqrt_rn(__dadd_rn(__dmul_rn(b, b), e)));
+  return __ddiv_rn(__dmul_rn(2.0, R), den);
+}
+
+__device__ __forceinline__ double tdep_integral(double beta, double t, double d) {
+  if (beta == 0.0) return d;
+  const double u = __dadd_rn(1.0, __dmul_rn(beta, t));
+  return __dadd_rn(__dmul_rn(d, u), __dmul_rn(__dmul_rn(__dmul_rn(beta, d), d), 0.5));
+}
+
 // The same from an already computed remainder rem = fl(P - T).
 __device__ __forceinline__ double waiting_time_rem(double rem, double a) {
   return dbits(rem) > 0 ? __ddiv_rn(rem, a) : 0.0;

@@ -444,22 +444,6 @@ __device__ __forceinline__ void simulate_rescaled(const RunArgs &A, const Thread
 // A_k I_k(t, d) = P_k - T_k, written without cancellation.  beta_k = 0 runs exactly the
 // constant-rate operations.
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ double tdep_wait(double A, double beta, double R, double t) {
-  if (!(dbits(R) > 0)) return 0.0;
-  if (beta == 0.0) return __ddiv_rn(R, A);
-  const double u = __dadd_rn(1.0, __dmul_rn(beta, t));
-  const double b = __dmul_rn(A, u);
-  const double e = __dmul_rn(__dmul_rn(__dmul_rn(2.0, A), beta), R);
-  const double den = __dadd_rn(b, __dsqrt_rn(__dadd_rn(__dmul_rn(b, b), e)));
-  return __ddiv_rn(__dmul_rn(2.0, R), den);
-}
-
-__device__ __forceinline__ double tdep_integral(double beta, double t, double d) {
-  if (beta == 0.0) return d;
-  const double u = __dadd_rn(1.0, __dmul_rn(beta, t));
-  return __dadd_rn(__dmul_rn(d, u), __dmul_rn(__dmul_rn(__dmul_rn(beta, d), d), 0.5));
-}
-
 template <int MAXM, bool LL>
 __device__ __forceinline__ void simulate_tdep(const RunArgs &A, const ThreadNet &S, const double *beta, const int64_t j,
                                               const int B, const int tend_finite, const int smem_mom) {

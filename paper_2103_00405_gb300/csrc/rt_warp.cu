@@ -64,6 +64,223 @@ __global__ void __launch_bounds__(kWarpBlock, R >= 8 ? 4 : 1)
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Time-dependent rates c_k(t) = c_k (1 + beta_k t) (Sec. 6, Eq. 29) for networks of up to
+// 256 reactions: a warp per trajectory, channel k in lane k % 32, register slot k / 32.
+// Every waiting time is the root of its channel's own integral, computed exactly (the
+// float-bound filter of the constant-rate routines is for plain quotients only); a warp
+// shuffle on (waiting time bits, channel) gives the smallest, smallest index on ties.  The
+// same operations, in the same order per channel, as the one-thread routine, so the results
+// are bit-identical to it and to the oracle.
+// ---------------------------------------------------------------------------------
+template <int R, bool LL>
+__global__ void __launch_bounds__(kWarpBlock) k_ens_tdep_warp(const RunArgs A, const int tend_finite) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr unsigned FULL = 0xFFFFFFFFu;
+  const DevNet &d = A.net;
+  const int M = d.M, N = d.N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t j = (int64_t)blockIdx.x * (kWarpBlock / 32) + warp;
+  if (j >= A.n_traj) return;  // whole warps only; the kernel has no block-wide barrier
+  int *X = (int *)smem + (size_t)warp * N;
+  auto xat = [&](int sp) { return X[sp]; };
+  const uint64_t g = (uint64_t)(A.traj_offset + j);
+  const int32_t *x0 = A.x0 + (A.per_traj_x0 ? j * (int64_t)N : 0);
+  bool badl = false;
+  for (int sp = lane; sp < N; sp += 32) {
+    const int v = x0[sp];
+    X[sp] = v;
+    badl |= v < 0;
+  }
+  const bool bad = __any_sync(FULL, badl);
+  __syncwarp();
+  double P[R], T[R], a[R], bt[R];
+  int32_t n[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int k = lane + 32 * r;
+    n[r] = 0;
+    T[r] = 0.0;
+    P[r] = 0.0;
+    a[r] = 0.0;
+    bt[r] = k < M ? d.beta[k] : 0.0;
+    if (!bad && k < M) {
+      P[r] = exp1_draw(A.seed, g, (uint32_t)k, 0u, A.stream_id);
+      a[r] = propensity(d.rdesc[k], d.c[k], xat);
+    }
+  }
+  int status = bad ? RT_TRAJ_BAD_X0 : RT_TRAJ_TEND;
+  double t = 0.0, ll = 0.0;
+  int32_t ev = 0;
+  int64_t gi = 0;
+  double next_g = 0.0;
+  auto record = [&](int64_t gidx, bool known) {
+    if (A.out.grid_dev) {
+      int32_t *gp = A.out.grid_dev + (j * A.G + gidx) * N;
+      for (int sp = lane; sp < N; sp += 32) gp[sp] = known ? X[sp] : -1;
+    }
+    if (!known || !A.out.grid_sum_dev) return;
+    for (int sp = lane; sp < N; sp += 32) {
+      const long long x = X[sp];
+      atomicAdd((unsigned long long *)(A.out.grid_sum_dev + gidx * N + sp), (unsigned long long)x);
+      if (A.out.grid_sumsq_dev)
+        atomicAdd((unsigned long long *)(A.out.grid_sumsq_dev + gidx * N + sp), (unsigned long long)(x * x));
+    }
+    if (lane == 0 && A.out.grid_count_dev) atomicAdd((unsigned long long *)(A.out.grid_count_dev + gidx), 1ull);
+  };
+  if (!bad) {
+    const int64_t tend_bits = dbits(A.t_end);
+    for (;;) {
+      int64_t best = kInfBits;
+      int kb = INT_MAX;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int k = lane + 32 * r;
+        if (k < M && dbits(a[r]) != 0) {
+          const int64_t wb = dbits(tdep_wait(a[r], bt[r], __dsub_rn(P[r], T[r]), t));
+          if (wb < best) {
+            best = wb;
+            kb = k;
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const int64_t w2 = __shfl_xor_sync(FULL, best, o);
+        const int k2 = __shfl_xor_sync(FULL, kb, o);
+        if (w2 < best || (w2 == best && k2 < kb)) {
+          best = w2;
+          kb = k2;
+        }
+      }
+      if (kb == INT_MAX) {
+        status = RT_TRAJ_ABSORBED;
+        break;
+      }
+      const double dmin = bitsd(best);
+      const double tn = __dadd_rn(t, dmin);
+      if (dbits(tn) > tend_bits) {
+        status = RT_TRAJ_TEND;
+        break;
+      }
+      if (ev == A.max_events) {
+        status = RT_TRAJ_MAX_EVENTS;
+        break;
+      }
+      const int vb = d.vptr[kb], ve = d.vptr[kb + 1];
+      bool over = false;
+      for (int i = vb + lane; i < ve; i += 32) {
+        const int2 e = d.vlist[i];
+        const long long nx = (long long)X[e.x] + e.y;
+        over |= (nx > INT_MAX) | (nx < 0);
+      }
+      if (__any_sync(FULL, over)) {
+        status = RT_TRAJ_OVERFLOW;
+        break;
+      }
+      while (gi < A.G && dbits(next_g) < dbits(tn)) {
+        record(gi, true);
+        ++gi;
+        next_g = __dmul_rn(__ll2double_rn(gi), A.sample_dt);
+      }
+      const double tprev = t;
+      t = tn;
+      if (lane == 0) trace_event(A.out, j, ev, kb, tn);
+      const int ol = kb & 31, os = kb >> 5;
+      const double a_mu = __shfl_sync(FULL, pick<R>(a, os), ol);
+      const double b_mu = __shfl_sync(FULL, pick<R>(bt, os), ol);
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (lane + 32 * r < M) T[r] = __dadd_rn(T[r], __dmul_rn(a[r], tdep_integral(bt[r], tprev, dmin)));
+      if (LL && lane == 0) ll = __dadd_rn(ll, rt_ln(__dmul_rn(a_mu, __dadd_rn(1.0, __dmul_rn(b_mu, t)))));
+      __syncwarp();  // every read of the pre-event X is done
+      for (int i = vb + lane; i < ve; i += 32) {
+        const int2 e = d.vlist[i];
+        X[e.x] += e.y;  // the species of one reaction are distinct
+      }
+      __syncwarp();
+      if (lane == ol) {
+        int32_t nmu = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (r == os) {
+            n[r] += 1;
+            nmu = n[r];
+          }
+        const double E = exp1_draw(A.seed, g, (uint32_t)kb, (uint32_t)nmu, A.stream_id);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (r == os) P[r] = __dadd_rn(P[r], E);
+      }
+      ++ev;
+      const uint32_t dm = d.depw[(size_t)kb * 32 + lane];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if ((dm >> r) & 1u) a[r] = propensity(d.rdesc[lane + 32 * r], d.c[lane + 32 * r], xat);
+    }
+  }
+  const bool known = status == RT_TRAJ_TEND || status == RT_TRAJ_ABSORBED;
+  for (; gi < A.G; ++gi) record(gi, known);
+  if (A.out.loglik_dev || A.out.t_internal_dev) {
+    if (known && tend_finite && !bad) {
+      const double rest = __dsub_rn(A.t_end, t);
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (lane + 32 * r < M) T[r] = __dadd_rn(T[r], __dmul_rn(a[r], tdep_integral(bt[r], t, rest)));
+    }
+    if (A.out.t_internal_dev)
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (lane + 32 * r < M) A.out.t_internal_dev[j * M + lane + 32 * r] = T[r];
+    if (A.out.loglik_dev) {
+      const double sT = warp_sum_T_in_order<R, 32>(T, M, true);  // sum_k T_k in k order
+      if (lane == 0) A.out.loglik_dev[j] = bad ? __longlong_as_double(0x7FF8000000000000ll) : __dsub_rn(ll, sT);
+    }
+  }
+  if (A.out.counts_dev)
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (lane + 32 * r < M) A.out.counts_dev[j * M + lane + 32 * r] = n[r];
+  if (A.out.x_final_dev)
+    for (int sp = lane; sp < N; sp += 32) A.out.x_final_dev[j * N + sp] = X[sp];
+  trace_tail(A.out, j, ev, lane, 32);
+  if (lane == 0) {
+    if (A.out.n_events_dev) A.out.n_events_dev[j] = ev;
+    if (A.out.status_dev) A.out.status_dev[j] = status;
+    if (A.out.t_last_dev) A.out.t_last_dev[j] = t;
+  }
+}
+
+template <int R>
+static cudaError_t launch_tdep_r(const RunArgs &a, cudaStream_t s, int tend_finite) {
+  const size_t smem = (size_t)a.net.N * 4 * (kWarpBlock / 32);
+  const unsigned grid = (unsigned)((a.n_traj + kWarpBlock / 32 - 1) / (kWarpBlock / 32));
+  auto kern = a.out.loglik_dev ? k_ens_tdep_warp<R, true> : k_ens_tdep_warp<R, false>;
+  raise_smem_limit((const void *)kern, smem);
+  kern<<<grid, kWarpBlock, smem, s>>>(a, tend_finite);
+  return cudaGetLastError();
+}
+
+int launch_tdep_warp_mapping(const RunArgs &a, int lanes_per_traj, cudaStream_t s) {
+  if (a.n_traj == 0) return RT_OK;
+  const int M = a.net.M;
+  if (lanes_per_traj != 0 && lanes_per_traj != 32)
+    return set_error(RT_ERR_UNSUPPORTED, "time-dependent rates on the warp mapping use 32 lanes per trajectory");
+  if (M > 256 || !a.net.depw || !a.net.beta)
+    return set_error(RT_ERR_UNSUPPORTED, "time-dependent rates run on the warp mapping with M <= 256 (got %d)", M);
+  if ((size_t)a.net.N * 4 * (kWarpBlock / 32) > 200 * 1024)
+    return set_error(RT_ERR_UNSUPPORTED, "warp mapping: too many species for shared memory");
+  const int tf = std::isfinite(a.t_end) ? 1 : 0;
+  const int need = (M + 31) / 32;
+  cudaError_t e;
+  if (need <= 1) e = launch_tdep_r<1>(a, s, tf);
+  else if (need <= 2) e = launch_tdep_r<2>(a, s, tf);
+  else if (need <= 4) e = launch_tdep_r<4>(a, s, tf);
+  else e = launch_tdep_r<8>(a, s, tf);
+  if (e != cudaSuccess) return set_error(RT_ERR_CUDA, "time-dependent warp kernel launch: %s", cudaGetErrorString(e));
+  return RT_OK;
+}
+
 int warp_mapping_max_m() { return 256; }
 
 static size_t warp_net_bytes(const DevNet &d, int G) {

@@ -1,5 +1,6 @@
 """Time-dependent rates c_k(t) = c_k (1 + beta_k t) (Sec. 6, Eq. 29; rt_network_set_rate_slopes)
-on the thread mapping against the oracle, bit for bit, through the C ABI."""
+on the thread mapping (M <= 16) and the warp mapping (M <= 256) against the oracle, bit for bit,
+through the C ABI."""
 import math
 
 import numpy as np
@@ -43,6 +44,37 @@ def test_ramped_rates_bit_exact(M, N):
     assert_trace(g, o)
 
 
+@pytest.mark.parametrize("M,N", [(17, 6), (40, 10), (64, 16), (100, 30), (256, 64)])
+def test_ramped_rates_on_the_warp_mapping_bit_exact(M, N):
+    """Networks above 16 reactions run a warp per trajectory by default (trace, grid, counts,
+    internal times, likelihood); then moments under an event cap on the explicitly requested warp
+    mapping."""
+    net = W.random_mass_action(N, M, seed=950 + M, c_sigma=0.6)
+    rng = np.random.default_rng(M)
+    beta = np.where(rng.random(M) < 0.3, 0.0, rng.uniform(0.1, 3.0, M))
+    x0 = W.poisson_x0(N, 25, M)
+    n = 67  # a ragged last block of warps
+    netg = api.Network(net).set_rate_slopes(beta)
+    t_end = 0.6 if M <= 64 else 0.25
+    g = api.simulate(netg, x0, t_end, n, seed=M, stream_id=1, traj_offset=5, max_events=100000, grad=True,
+                     grid="traj", sample_dt=0.05, trace_len=300)
+    o = oracle.run(net, x0, t_end, n, seed=M, stream_id=1, traj_offset=5, max_events=100000, want_grad=True,
+                   want_grid=True, sample_dt=0.05, trace_len=300, beta=beta, n_threads=16)
+    assert o["n_events"].mean() > 10
+    assert_same(g, o)
+    assert_trace(g, o)
+    # moments, event cap and an explicit warp mapping
+    m = api.simulate(netg, x0, t_end, n, seed=M, max_events=40, sample_dt=0.05, grid="moments",
+                     mapping=L.RT_MAP_WARP, lanes_per_traj=32)
+    om = oracle.run(net, x0, t_end, n, seed=M, max_events=40, sample_dt=0.05, want_grid=True, beta=beta,
+                    n_threads=16)
+    grid = om["grid"].astype(np.int64)
+    known = grid >= 0
+    assert np.array_equal(m["grid_sum"].cpu().numpy(), np.where(known, grid, 0).sum(0))
+    assert np.array_equal(m["grid_count"].cpu().numpy(), known[:, :, 0].sum(0))
+    assert np.array_equal(m["n_events"].cpu().numpy(), om["n_events"])
+
+
 def test_zero_slopes_give_the_constant_rate_path_and_moments():
     net = W.random_mass_action(5, 9, seed=95)
     x0 = W.poisson_x0(5, 20, 96)
@@ -68,8 +100,12 @@ def test_zero_slopes_give_the_constant_rate_path_and_moments():
 def test_time_dependent_rates_are_refused_where_unsupported():
     netg = api.Network(W.random_mass_action(10, 40, seed=97)).set_rate_slopes(np.full(40, 0.5))
     x0 = W.poisson_x0(10, 20, 1)
-    for kw in (dict(mapping=L.RT_MAP_WARP), dict(mapping=L.RT_MAP_BLOCK), dict(form=L.RT_FORM_ABSOLUTE)):
+    for kw in (dict(mapping=L.RT_MAP_THREAD), dict(mapping=L.RT_MAP_BLOCK), dict(form=L.RT_FORM_ABSOLUTE),
+               dict(form=L.RT_FORM_RESCALED), dict(mapping=L.RT_MAP_WARP, lanes_per_traj=8)):
         with pytest.raises(L.RandtimeError):
             api.simulate(netg, x0, 1.0, 2, **kw)
+    big = api.Network(W.random_mass_action(60, 300, seed=98)).set_rate_slopes(np.full(300, 0.5))
+    with pytest.raises(L.RandtimeError):
+        api.simulate(big, W.poisson_x0(60, 20, 1), 1.0, 2)
     with pytest.raises(L.RandtimeError):
         api.Network(W.birth_death()).set_rate_slopes([-1.0, 0.0])
