@@ -59,9 +59,9 @@ FP64_OP_NOMINAL = 0.625e12
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch over the units it
 # processed).  A kernel changed since its capture must have its entry set to None.
 NCU_TRAFFIC = {
-    "k_bundle": dict(bytes_per_unit=(77561792000 + 25620354048) / (200 * 16 * 1e6), unit="channel-event",
+    "k_bundle": dict(bytes_per_unit=(77562891264 + 25620826880) / (200 * 16 * 1e6), unit="channel-event",
                      source="ncu capture of k_bundle<false>, N=1e4, M=1e6, 16 trajectories x 200 events"),
-    "k_ens_small": dict(bytes_per_unit=(830464 + 0) / 16384, unit="trajectory",
+    "k_ens_small": dict(bytes_per_unit=(818944 + 0) / 16384, unit="trajectory",
                         source="ncu capture of k_ens_small<3,2,false>, 16384 Lotka-Volterra trajectories to t=10"),
 }
 
