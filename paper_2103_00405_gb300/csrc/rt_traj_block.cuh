@@ -9,10 +9,10 @@
 //      its internal times with the pre-event propensities (Eq. 17), recomputes the
 //      marked propensities (Eq. 1-2) and proposes its smallest certified upper
 //      bound of the waiting time;
-//   3. each warp's best candidate is computed exactly by its owner and published with
-//      the warp's bound; every thread takes the block's best candidate from those, computes
-//      exactly only channels not certified to be larger, and a block reduction on
-//      (waiting time bits, channel) gives the exact argmin (Eq. 25-26).
+//   3. each warp's best candidate publishes a float upper bound of its waiting time; every
+//      thread takes the block's best candidate's bound as threshold, computes exactly only
+//      channels not certified to be larger, and a block reduction on (waiting time bits,
+//      channel) gives the exact argmin (Eq. 25-26).
 #pragma once
 #include <climits>
 
@@ -38,7 +38,7 @@ struct BlockScratch {
   float *red_u;     // [warps]
   int *red_k;       // [warps]
   long long *red_w; // [warps]
-  long long *red_x; // [warps] exact waiting time (bits) of each warp's candidate
+  float *red_q;     // [warps] float upper bound of each warp's candidate's waiting time
   int *red_k2;      // [warps]
   double *buf;      // [B] (and the broadcast slots below)
   long long *s_wc;  // candidate's exact waiting time
@@ -49,7 +49,7 @@ struct BlockScratch {
 
 __host__ __device__ inline size_t block_scratch_bytes(int M, int N, int B) {
   const int W = B / 32;
-  return (size_t)N * 4 + (size_t)M * 4 + (size_t)((M + 31) / 32) * 4 + (size_t)W * (4 + 4 + 8 + 8 + 4) +
+  return (size_t)N * 4 + (size_t)M * 4 + (size_t)((M + 31) / 32) * 4 + (size_t)W * (4 + 4 + 4 + 8 + 4) +
          (size_t)B * 8 + 32 + 64;
 }
 
@@ -58,12 +58,12 @@ __device__ inline BlockScratch carve_block_scratch(unsigned char *base, int M, i
   BlockScratch s;
   s.buf = (double *)base;
   s.red_w = (long long *)(s.buf + B);
-  s.red_x = s.red_w + W;
-  s.s_wc = s.red_x + W;
+  s.s_wc = s.red_w + W;
   s.s_amu = (double *)(s.s_wc + 1);
   s.s_E = s.s_amu + 1;
   s.red_u = (float *)(s.s_E + 1);
-  s.red_k = (int *)(s.red_u + W);
+  s.red_q = s.red_u + W;
+  s.red_k = (int *)(s.red_q + W);
   s.red_k2 = s.red_k + W;
   s.s_over = s.red_k2 + W;
   s.bm = (uint32_t *)(s.s_over + 1);
@@ -178,11 +178,11 @@ __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNe
           kub = k2;
         }
       }
-      // the warp candidate's owner computes its exact waiting time now, so the block's
-      // candidate is known exactly right after the reduction (one barrier, not two)
+      // the warp candidate's owner publishes a float upper bound of its waiting time with it, so
+      // the block's threshold is known right after the reduction (one barrier, no division)
       if (kub != INT_MAX && tid == kub % B) {
         const int rs = kub / B;
-        S.red_x[warp] = dbits(waiting_time(pick<R>(P, rs), pick<R>(T, rs), pick<R>(a, rs)));
+        S.red_q[warp] = quot_upper(pick<R>(P, rs), pick<R>(T, rs), pick<R>(a, rs));
         S.red_u[warp] = ub;
         S.red_k[warp] = kub;
       } else if (kub == INT_MAX && lane == 0) {
@@ -207,16 +207,15 @@ __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNe
         status = RT_TRAJ_ABSORBED;
         break;
       }
-      // ---- the best candidate exactly (from its warp's slot), then every channel not certified
-      // larger (Eq. 25-26)
-      const long long wc = S.red_x[(kub % B) >> 5];
-      const float thr = f32_upper(bitsd(wc));
-      long long bw = wc;
-      int bk = kub;
+      // ---- every channel not certified to lie above the block candidate's upper bound, exactly
+      // (the candidate itself is never certified above its own bound) (Eq. 25-26)
+      const float thr = S.red_q[(kub % B) >> 5];
+      long long bw = LLONG_MAX;
+      int bk = INT_MAX;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int k = tid + B * r;
-        if (k < M && k != kub && dbits(a[r]) != 0 && !exceeds(P[r], T[r], a[r], thr)) {
+        if (k < M && dbits(a[r]) != 0 && !exceeds(P[r], T[r], a[r], thr)) {
           const long long wb = dbits(waiting_time(P[r], T[r], a[r]));
           if (wb < bw || (wb == bw && k < bk)) {
             bw = wb;
