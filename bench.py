@@ -290,7 +290,7 @@ def cpu_baseline(cfgs, sample):
 def cpu_other_configs():
     """The oracle on bounded samples of the other configurations: the ensemble on one core, the
     large network (one trajectory, 200 events: each event recomputes and scans all 10^6 channels),
-    the gradient network with the likelihood (256 trajectories on every core)."""
+    the gradient network with the likelihood (8192 trajectories on every core)."""
     import oracle
     threads = os.cpu_count() or 1
     out = {}
@@ -309,9 +309,9 @@ def cpu_other_configs():
     big = W.large_network_config(max_events=200)
     timed("large_network", (1, "1 trajectory x 200 events of the N=1e4, M=1e6 network, one thread"),
           lambda: int(oracle.run(big["net"], big["x0"], big["t_end"], 1, seed=1, max_events=200)["n_events"].sum()))
-    gc = W.grad_config(256)
-    timed("gradient", (threads, "256 trajectories of the M=64 gradient network to t_end=5 with the likelihood"),
-          lambda: int(oracle.run(gc["net"], gc["x0"], gc["t_end"], 256, seed=1, want_grad=True,
+    gc = W.grad_config(8192)
+    timed("gradient", (threads, "8192 trajectories of the M=64 gradient network to t_end=5 with the likelihood"),
+          lambda: int(oracle.run(gc["net"], gc["x0"], gc["t_end"], 8192, seed=1, want_grad=True,
                                  n_threads=threads)["n_events"].sum()))
     return out
 
@@ -656,7 +656,9 @@ def run_table3(args, ctx, steps, warmup):
     """The paper's own GPU formulation (Table 3: relative waiting times rescaled after every
     event, every propensity recomputed) against Table 2's internal-time form, on the model of the
     paper's Fig. 1 (Lotka-Volterra, Table 4 rates, X0 = Y0 = 1000), 2^18 trajectories to t_end = 10
-    per step, one thread per trajectory, the same trajectories both ways."""
+    per step, one thread per trajectory, the same trajectories both ways; then the same on the
+    gradient network (M = 64) with a warp per trajectory (Table 3's form, a lane per channel)
+    against warp segments (Table 2's form)."""
     import torch
 
     from paper_2103_00405_gb300 import _lib as L
@@ -683,6 +685,28 @@ def run_table3(args, ctx, steps, warmup):
                      "events_per_step": events_all / steps, "clocks": clocks,
                      "kernel": "k_ens_rescaled<3,false,true>" if form == L.RT_FORM_RESCALED
                      else "k_ens_small<3,2,false>"}
+    # the same comparison on a mid-size network (the gradient workload's M = 64, N = 16): Table 3's
+    # form with a lane per channel (the paper's thread-per-reaction layout) against Table 2's form
+    # on warp segments, 16384 trajectories to t_end = 5
+    gcfg = W.grad_config(16384)
+    gnet = api.Network(gcfg["net"])
+    gx0 = torch.as_tensor(gcfg["x0"], dtype=torch.int32).to(ctx.dev)
+    ng = gcfg["n_traj"]
+    mid = {}
+    for name, form in (("table3_rescaled_warp", L.RT_FORM_RESCALED), ("table2_internal_warp", L.RT_FORM_INTERNAL)):
+        outs = {}
+        step_events = []
+
+        def step(i, record):
+            outs.update(api.simulate(gnet, gx0, gcfg["t_end"], ng, seed=1, traj_offset=traj_base(ctx.rank, i, ng),
+                                     max_events=10**8, mapping=L.RT_MAP_WARP, form=form, outputs=outs))
+
+        ms, _, _ = timed_steps(ctx, step, steps, warmup,
+                               after=lambda i: step_events.append(int(outs["n_events"].sum().item())))
+        dev_ms, events_all = combine_over_ranks(sum(ms), sum(step_events), ctx.world, ctx.dev)
+        mid[name] = {"value": events_all / (dev_ms / 1e3), "unit": UNIT, "ms_per_step": dev_ms / steps,
+                     "kernel": "k_ens_rescaled_warp<2,false>" if form == L.RT_FORM_RESCALED
+                     else "k_ens_warp<8,8,false>"}
     line = {"value": res["table3_rescaled"]["value"], "unit": UNIT, "steps": steps, "warmup": warmup,
             "ms_per_step": res["table3_rescaled"]["ms_per_step"],
             "config": {"workload": "Table 3's form vs Table 2's internal-time form: Lotka-Volterra (Fig. 1 model, "
@@ -690,7 +714,10 @@ def run_table3(args, ctx, steps, warmup):
                                    "per trajectory, the same trajectories both ways",
                        "parallelism": "trajectories sharded over ranks" if ctx.world > 1 else "1 GPU"},
             "gpu_launches": steps, "forms": res,
-            "internal_over_rescaled": res["table2_internal"]["value"] / res["table3_rescaled"]["value"]}
+            "internal_over_rescaled": res["table2_internal"]["value"] / res["table3_rescaled"]["value"],
+            "mid_size": {"workload": "the gradient network (M=64, N=16), 16384 trajectories to t_end=5, warp mapping",
+                         "forms": mid, "internal_over_rescaled":
+                         mid["table2_internal_warp"]["value"] / mid["table3_rescaled_warp"]["value"]}}
     return line
 
 

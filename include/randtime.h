@@ -82,7 +82,8 @@ enum {
                            T_k += a_k (t - s_k), s_k = t, P_mu += E, a_k and tau_k recomputed;
                            at the end T_k += a_k (t_f - s_k) with t_f = t_end (run reached it)
                            or the last event time */
-  RT_FORM_RESCALED = 2  /* Table 3's form (thread mapping, M <= 8): relative waiting times w_k;
+  RT_FORM_RESCALED = 2  /* Table 3's form (thread mapping up to M = 8, warp mapping -- a warp per
+                           trajectory, a lane per channel -- up to M = 256): relative waiting times w_k;
                            after an event that took dt every propensity is recomputed and every
                            other waiting time rescaled, w_k = (p_k / a_k)(w_k - dt), p_k the
                            previous propensity; the fired channel draws w_mu = E / a_mu; a channel

@@ -19,7 +19,7 @@ int check_device(const rt_network *net) {
 static int choose_mapping(const rt_network *net, const rt_launch_cfg *cfg, int form = RT_FORM_INTERNAL) {
   if (cfg && cfg->mapping != RT_MAP_AUTO) return cfg->mapping;
   if (form == RT_FORM_ABSOLUTE) return RT_MAP_TREE;
-  if (form == RT_FORM_RESCALED) return RT_MAP_THREAD;
+  if (form == RT_FORM_RESCALED) return net->dev.M <= 8 ? RT_MAP_THREAD : RT_MAP_WARP;
   if (net->dev.M <= thread_mapping_max_m()) return RT_MAP_THREAD;
   if (net->dev.M <= warp_mapping_max_m()) return RT_MAP_WARP;
   if (net->dev.M <= block_mapping_max_m()) return RT_MAP_BLOCK;
@@ -104,8 +104,9 @@ extern "C" int rt_run(const rt_network *net, const rt_run_params *p, const rt_ou
                                     : launch_tdep_warp_mapping(a, cfg ? cfg->lanes_per_traj : 0, s);
   }
   if (p->form == RT_FORM_RESCALED) {
-    if (mapping != RT_MAP_THREAD) return set_error(RT_ERR_UNSUPPORTED, "Table 3's rescaled form runs on the thread mapping");
-    return launch_rescaled_mapping(a, B, s);
+    if (mapping == RT_MAP_THREAD) return launch_rescaled_mapping(a, B, s);
+    if (mapping == RT_MAP_WARP) return launch_rescaled_warp_mapping(a, cfg ? cfg->lanes_per_traj : 0, s);
+    return set_error(RT_ERR_UNSUPPORTED, "Table 3's rescaled form runs on the thread (M <= 8) or warp (M <= 256) mapping");
   }
   switch (mapping) {
     case RT_MAP_THREAD:

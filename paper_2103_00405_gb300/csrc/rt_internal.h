@@ -110,6 +110,7 @@ int launch_thread_mapping(const RunArgs &a, int block_threads, cudaStream_t s);
 int launch_rescaled_mapping(const RunArgs &a, int block_threads, cudaStream_t s);
 int launch_tdep_mapping(const RunArgs &a, int block_threads, cudaStream_t s);
 int launch_tdep_warp_mapping(const RunArgs &a, int lanes_per_traj, cudaStream_t s);
+int launch_rescaled_warp_mapping(const RunArgs &a, int lanes_per_traj, cudaStream_t s);
 int launch_small_mapping(const RunArgs &a, const SmallNet &net, int block_threads, cudaStream_t s);
 int thread_mapping_max_m();
 size_t bundle_workspace_bytes(const DevNet &net, int64_t n_traj, int ctas_per_traj);

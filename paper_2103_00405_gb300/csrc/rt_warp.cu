@@ -281,6 +281,231 @@ int launch_tdep_warp_mapping(const RunArgs &a, int lanes_per_traj, cudaStream_t 
   return RT_OK;
 }
 
+// ---------------------------------------------------------------------------------
+// Table 3's form ("parallel NRRTA", Sec. 5) for networks of up to 256 reactions: a warp per
+// trajectory, channel k in lane k % 32, register slot k / 32 -- the paper's own GPU layout of a
+// thread per reaction channel with a parallel reduction for the next reaction.  Per event every
+// propensity is recomputed (no dependency graph) and every other relative waiting time is
+// rescaled, w_k = (p_k / a_k)(w_k - dt); the fired channel draws w_mu = E / a_mu; a channel whose
+// propensity drops to 0 keeps its remaining internal time p_k (w_k - dt) until it can fire again.
+// The per-channel operations and their order are those of the one-thread routine.
+// ---------------------------------------------------------------------------------
+template <int R, bool LL>
+__global__ void __launch_bounds__(kWarpBlock) k_ens_rescaled_warp(const RunArgs A, const int tend_finite) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr unsigned FULL = 0xFFFFFFFFu;
+  const DevNet &d = A.net;
+  const int M = d.M, N = d.N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t j = (int64_t)blockIdx.x * (kWarpBlock / 32) + warp;
+  if (j >= A.n_traj) return;  // whole warps only; the kernel has no block-wide barrier
+  const bool want_T = A.out.loglik_dev || A.out.t_internal_dev;
+  int *X = (int *)smem + (size_t)warp * N;
+  auto xat = [&](int sp) { return X[sp]; };
+  const uint64_t g = (uint64_t)(A.traj_offset + j);
+  const int32_t *x0 = A.x0 + (A.per_traj_x0 ? j * (int64_t)N : 0);
+  bool badl = false;
+  for (int sp = lane; sp < N; sp += 32) {
+    const int v = x0[sp];
+    X[sp] = v;
+    badl |= v < 0;
+  }
+  const bool bad = __any_sync(FULL, badl);
+  __syncwarp();
+  double w[R], T[R], a[R];
+  int32_t n[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int k = lane + 32 * r;
+    n[r] = 0;
+    T[r] = 0.0;
+    w[r] = 0.0;
+    a[r] = 0.0;
+    if (!bad && k < M) {
+      const double E = exp1_draw(A.seed, g, (uint32_t)k, 0u, A.stream_id);
+      a[r] = propensity(d.rdesc[k], d.c[k], xat);
+      w[r] = dbits(a[r]) != 0 ? __ddiv_rn(E, a[r]) : E;  // frozen: the remaining internal time
+    }
+  }
+  int status = bad ? RT_TRAJ_BAD_X0 : RT_TRAJ_TEND;
+  double t = 0.0, ll = 0.0;
+  int32_t ev = 0;
+  int64_t gi = 0;
+  double next_g = 0.0;
+  auto record = [&](int64_t gidx, bool known) {
+    if (A.out.grid_dev) {
+      int32_t *gp = A.out.grid_dev + (j * A.G + gidx) * N;
+      for (int sp = lane; sp < N; sp += 32) gp[sp] = known ? X[sp] : -1;
+    }
+    if (!known || !A.out.grid_sum_dev) return;
+    for (int sp = lane; sp < N; sp += 32) {
+      const long long x = X[sp];
+      atomicAdd((unsigned long long *)(A.out.grid_sum_dev + gidx * N + sp), (unsigned long long)x);
+      if (A.out.grid_sumsq_dev)
+        atomicAdd((unsigned long long *)(A.out.grid_sumsq_dev + gidx * N + sp), (unsigned long long)(x * x));
+    }
+    if (lane == 0 && A.out.grid_count_dev) atomicAdd((unsigned long long *)(A.out.grid_count_dev + gidx), 1ull);
+  };
+  if (!bad) {
+    const int64_t tend_bits = dbits(A.t_end);
+    for (;;) {
+      // the smallest waiting time (ties: smallest index); frozen channels cannot fire
+      int64_t best = kInfBits;
+      int kb = INT_MAX;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int k = lane + 32 * r;
+        if (k < M && dbits(a[r]) != 0 && dbits(w[r]) < best) {
+          best = dbits(w[r]);
+          kb = k;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const int64_t w2 = __shfl_xor_sync(FULL, best, o);
+        const int k2 = __shfl_xor_sync(FULL, kb, o);
+        if (w2 < best || (w2 == best && k2 < kb)) {
+          best = w2;
+          kb = k2;
+        }
+      }
+      if (kb == INT_MAX) {
+        status = RT_TRAJ_ABSORBED;
+        break;
+      }
+      const double dmin = bitsd(best);
+      const double tn = __dadd_rn(t, dmin);
+      if (dbits(tn) > tend_bits) {
+        status = RT_TRAJ_TEND;
+        break;
+      }
+      if (ev == A.max_events) {
+        status = RT_TRAJ_MAX_EVENTS;
+        break;
+      }
+      const int vb = d.vptr[kb], ve = d.vptr[kb + 1];
+      bool over = false;
+      for (int i = vb + lane; i < ve; i += 32) {
+        const int2 e = d.vlist[i];
+        const long long nx = (long long)X[e.x] + e.y;
+        over |= (nx > INT_MAX) | (nx < 0);
+      }
+      if (__any_sync(FULL, over)) {
+        status = RT_TRAJ_OVERFLOW;
+        break;
+      }
+      while (gi < A.G && dbits(next_g) < dbits(tn)) {
+        record(gi, true);
+        ++gi;
+        next_g = __dmul_rn(__ll2double_rn(gi), A.sample_dt);
+      }
+      t = tn;
+      if (lane == 0) trace_event(A.out, j, ev, kb, tn);
+      const int ol = kb & 31, os = kb >> 5;
+      const double a_mu = __shfl_sync(FULL, pick<R>(a, os), ol);
+      if (want_T)
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (lane + 32 * r < M) T[r] = __dadd_rn(T[r], __dmul_rn(a[r], dmin));
+      if (LL && lane == 0) ll = __dadd_rn(ll, rt_ln(a_mu));
+      __syncwarp();  // every read of the pre-event X is done
+      for (int i = vb + lane; i < ve; i += 32) {
+        const int2 e = d.vlist[i];
+        X[e.x] += e.y;  // the species of one reaction are distinct
+      }
+      __syncwarp();
+      double E = 0.0;
+      if (lane == ol) {
+        int32_t nmu = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (r == os) {
+            n[r] += 1;
+            nmu = n[r];
+          }
+        E = exp1_draw(A.seed, g, (uint32_t)kb, (uint32_t)nmu, A.stream_id);
+      }
+      ++ev;
+      // recalculate every propensity; rescale every other waiting time; the fired one redraws
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int k = lane + 32 * r;
+        if (k < M) {
+          const double an = propensity(d.rdesc[k], d.c[k], xat);
+          if (k == kb) {
+            w[r] = dbits(an) != 0 ? __ddiv_rn(E, an) : E;
+          } else if (dbits(a[r]) != 0) {
+            const double rem = __dsub_rn(w[r], dmin);
+            w[r] = dbits(an) != 0 ? __dmul_rn(__ddiv_rn(a[r], an), rem) : __dmul_rn(a[r], rem);
+          } else if (dbits(an) != 0) {
+            w[r] = __ddiv_rn(w[r], an);  // a frozen channel resumes
+          }
+          a[r] = an;
+        }
+      }
+    }
+  }
+  const bool known = status == RT_TRAJ_TEND || status == RT_TRAJ_ABSORBED;
+  for (; gi < A.G; ++gi) record(gi, known);
+  if (want_T) {
+    if (known && tend_finite && !bad) {
+      const double rest = __dsub_rn(A.t_end, t);
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (lane + 32 * r < M) T[r] = __dadd_rn(T[r], __dmul_rn(a[r], rest));
+    }
+    if (A.out.t_internal_dev)
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (lane + 32 * r < M) A.out.t_internal_dev[j * M + lane + 32 * r] = T[r];
+    if (A.out.loglik_dev) {
+      const double sT = warp_sum_T_in_order<R, 32>(T, M, true);  // sum_k T_k in k order
+      if (lane == 0) A.out.loglik_dev[j] = bad ? __longlong_as_double(0x7FF8000000000000ll) : __dsub_rn(ll, sT);
+    }
+  }
+  if (A.out.counts_dev)
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (lane + 32 * r < M) A.out.counts_dev[j * M + lane + 32 * r] = n[r];
+  if (A.out.x_final_dev)
+    for (int sp = lane; sp < N; sp += 32) A.out.x_final_dev[j * N + sp] = X[sp];
+  trace_tail(A.out, j, ev, lane, 32);
+  if (lane == 0) {
+    if (A.out.n_events_dev) A.out.n_events_dev[j] = ev;
+    if (A.out.status_dev) A.out.status_dev[j] = status;
+    if (A.out.t_last_dev) A.out.t_last_dev[j] = t;
+  }
+}
+
+template <int R>
+static cudaError_t launch_rescaled_r(const RunArgs &a, cudaStream_t s, int tend_finite) {
+  const size_t smem = (size_t)a.net.N * 4 * (kWarpBlock / 32);
+  const unsigned grid = (unsigned)((a.n_traj + kWarpBlock / 32 - 1) / (kWarpBlock / 32));
+  auto kern = a.out.loglik_dev ? k_ens_rescaled_warp<R, true> : k_ens_rescaled_warp<R, false>;
+  raise_smem_limit((const void *)kern, smem);
+  kern<<<grid, kWarpBlock, smem, s>>>(a, tend_finite);
+  return cudaGetLastError();
+}
+
+int launch_rescaled_warp_mapping(const RunArgs &a, int lanes_per_traj, cudaStream_t s) {
+  if (a.n_traj == 0) return RT_OK;
+  const int M = a.net.M;
+  if (lanes_per_traj != 0 && lanes_per_traj != 32)
+    return set_error(RT_ERR_UNSUPPORTED, "Table 3's form on the warp mapping uses 32 lanes per trajectory");
+  if (M > 256) return set_error(RT_ERR_UNSUPPORTED, "Table 3's form runs on the warp mapping with M <= 256 (got %d)", M);
+  if ((size_t)a.net.N * 4 * (kWarpBlock / 32) > 200 * 1024)
+    return set_error(RT_ERR_UNSUPPORTED, "warp mapping: too many species for shared memory");
+  const int tf = std::isfinite(a.t_end) ? 1 : 0;
+  const int need = (M + 31) / 32;
+  cudaError_t e;
+  if (need <= 1) e = launch_rescaled_r<1>(a, s, tf);
+  else if (need <= 2) e = launch_rescaled_r<2>(a, s, tf);
+  else if (need <= 4) e = launch_rescaled_r<4>(a, s, tf);
+  else e = launch_rescaled_r<8>(a, s, tf);
+  if (e != cudaSuccess) return set_error(RT_ERR_CUDA, "Table 3 warp kernel launch: %s", cudaGetErrorString(e));
+  return RT_OK;
+}
+
 int warp_mapping_max_m() { return 256; }
 
 static size_t warp_net_bytes(const DevNet &d, int G) {

@@ -1,6 +1,6 @@
 """Table 3's form of the method (relative waiting times rescaled by p_k / a_k after every event,
-every propensity recomputed; RT_FORM_RESCALED on the thread mapping) against the oracle's mode 2,
-bit for bit, through the C ABI."""
+every propensity recomputed; RT_FORM_RESCALED on the thread mapping up to 8 reactions and on a warp
+per trajectory up to 256) against the oracle's mode 2, bit for bit, through the C ABI."""
 import math
 
 import numpy as np
@@ -53,6 +53,29 @@ def test_rescaled_form_bit_exact(name):
     assert_trace(g, o)
 
 
+@pytest.mark.parametrize("M,N", [(9, 4), (33, 10), (64, 16), (150, 40), (256, 64)])
+def test_rescaled_form_on_the_warp_mapping_bit_exact(M, N):
+    net = W.random_mass_action(N, M, seed=970 + M, c_sigma=0.6)
+    x0 = W.poisson_x0(N, 25, M)
+    n = 45  # a ragged last block of warps
+    t_end = 0.5 if M <= 64 else 0.2
+    netg = api.Network(net)
+    g = api.simulate(netg, x0, t_end, n, seed=M, stream_id=3, traj_offset=2, max_events=100000, grad=True,
+                     grid="traj", sample_dt=t_end / 10, trace_len=300, **RES)
+    o = oracle.run(net, x0, t_end, n, seed=M, stream_id=3, traj_offset=2, max_events=100000, want_grad=True,
+                   want_grid=True, sample_dt=t_end / 10, trace_len=300, n_threads=16, **MODE)
+    assert o["n_events"].mean() > 10
+    assert_same(g, o)
+    assert_trace(g, o)
+    # the warp kernel on a small network too (explicit mapping), with an event cap
+    small = W.random_mass_action(4, 5, seed=92)
+    xs = W.poisson_x0(4, 30, 3)
+    gs = api.simulate(api.Network(small), xs, 0.5, 70, seed=2, max_events=25, grad=True, mapping=L.RT_MAP_WARP,
+                      **RES)
+    os_ = oracle.run(small, xs, 0.5, 70, seed=2, max_events=25, want_grad=True, n_threads=16, **MODE)
+    assert_same(gs, os_)
+
+
 def test_rescaled_form_moments_and_absorption():
     net, x0 = W.dimerisation(), np.array([1000, 0], np.int32)
     netg = api.Network(net)
@@ -70,7 +93,13 @@ def test_rescaled_form_moments_and_absorption():
 
 def test_rescaled_form_limits():
     netg = api.Network(W.random_mass_action(6, 12, seed=93))
+    x0 = W.poisson_x0(6, 10, 1)
     with pytest.raises(L.RandtimeError):
-        api.simulate(netg, W.poisson_x0(6, 10, 1), 1.0, 4, **RES)  # M > 8
+        api.simulate(netg, x0, 1.0, 4, mapping=L.RT_MAP_THREAD, **RES)  # M > 8 on the thread mapping
     with pytest.raises(L.RandtimeError):
-        api.simulate(api.Network(W.birth_death()), [0], 1.0, 4, mapping=L.RT_MAP_WARP, **RES)
+        api.simulate(netg, x0, 1.0, 4, mapping=L.RT_MAP_BLOCK, **RES)
+    with pytest.raises(L.RandtimeError):
+        api.simulate(netg, x0, 1.0, 4, mapping=L.RT_MAP_WARP, lanes_per_traj=8, **RES)
+    big = api.Network(W.random_mass_action(60, 300, seed=94))
+    with pytest.raises(L.RandtimeError):
+        api.simulate(big, W.poisson_x0(60, 10, 1), 1.0, 4, **RES)  # M > 256
