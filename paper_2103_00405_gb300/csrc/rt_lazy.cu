@@ -770,6 +770,7 @@ int launch_lazy_mapping(const RunArgs &a, int max_dependents, int ctas_per_traj,
     return set_error(RT_ERR_OOM, "absolute-time form needs %zu bytes of workspace (got %zu)", p.total, ws_bytes);
   if (((uintptr_t)ws & 255) != 0) return set_error(RT_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
   // every check before the first enqueued operation
+  if (a.n_traj * C > INT_MAX) return set_error(RT_ERR_UNSUPPORTED, "absolute-time form: too many trajectories for one launch");
   if (lazy_active_clusters(p, ll) < 1)
     return set_error(RT_ERR_UNSUPPORTED, "absolute-time form: a cluster of %d CTAs cannot be resident", C);
   char *w = (char *)ws;

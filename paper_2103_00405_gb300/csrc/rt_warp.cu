@@ -270,6 +270,8 @@ int launch_tdep_warp_mapping(const RunArgs &a, int lanes_per_traj, cudaStream_t 
     return set_error(RT_ERR_UNSUPPORTED, "time-dependent rates run on the warp mapping with M <= 256 (got %d)", M);
   if ((size_t)a.net.N * 4 * (kWarpBlock / 32) > 200 * 1024)
     return set_error(RT_ERR_UNSUPPORTED, "warp mapping: too many species for shared memory");
+  if ((a.n_traj + kWarpBlock / 32 - 1) / (kWarpBlock / 32) > INT_MAX)
+    return set_error(RT_ERR_UNSUPPORTED, "warp mapping: too many trajectories for one launch");
   const int tf = std::isfinite(a.t_end) ? 1 : 0;
   const int need = (M + 31) / 32;
   cudaError_t e;
@@ -495,6 +497,8 @@ int launch_rescaled_warp_mapping(const RunArgs &a, int lanes_per_traj, cudaStrea
   if (M > 256) return set_error(RT_ERR_UNSUPPORTED, "Table 3's form runs on the warp mapping with M <= 256 (got %d)", M);
   if ((size_t)a.net.N * 4 * (kWarpBlock / 32) > 200 * 1024)
     return set_error(RT_ERR_UNSUPPORTED, "warp mapping: too many species for shared memory");
+  if ((a.n_traj + kWarpBlock / 32 - 1) / (kWarpBlock / 32) > INT_MAX)
+    return set_error(RT_ERR_UNSUPPORTED, "warp mapping: too many trajectories for one launch");
   const int tf = std::isfinite(a.t_end) ? 1 : 0;
   const int need = (M + 31) / 32;
   cudaError_t e;
@@ -544,6 +548,9 @@ int launch_warp_mapping(const RunArgs &a, int block_threads, int lanes_per_traj,
   if (!dep) return set_error(RT_ERR_UNSUPPORTED, "warp mapping: no dependency table for %d lanes", G);
   const size_t smem = warp_net_bytes(a.net, G) + (size_t)a.net.N * 4 * (kWarpBlock / 32) * (32 / G);
   if (smem > 200 * 1024) return set_error(RT_ERR_UNSUPPORTED, "warp mapping: network too large for shared memory");
+  const int64_t per_block = (int64_t)(kWarpBlock / 32) * (32 / G);
+  if ((a.n_traj + per_block - 1) / per_block > INT_MAX)
+    return set_error(RT_ERR_UNSUPPORTED, "warp mapping: too many trajectories for one launch");
   const int tf = std::isfinite(a.t_end) ? 1 : 0;
   const int need = (M + G - 1) / G;
   cudaError_t e;
