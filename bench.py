@@ -63,6 +63,8 @@ NCU_TRAFFIC = {
                      source="ncu capture of k_bundle<false>, N=1e4, M=1e6, 16 trajectories x 200 events"),
     "k_ens_small": dict(bytes_per_unit=(818944 + 0) / 16384, unit="trajectory",
                         source="ncu capture of k_ens_small<3,2,false>, 16384 Lotka-Volterra trajectories to t=10"),
+    "k_lazy": dict(bytes_per_unit=(2468666880 + 874632704) / (16 * 2000), unit="event",
+                   source="ncu capture of k_lazy<false>, N=1e4, M=1e6, 16 trajectories x 2000 events"),
 }
 
 
@@ -644,7 +646,11 @@ def run_large_tree(args, ctx, steps, warmup):
             "events_per_step": events_all / steps, "clocks": clocks, "gpu_launches": 2 * steps,
             "us_per_event_per_trajectory": statistics.mean(ms) * 1e3 / ev_per_traj,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "kernel": "k_lazy<false>", "bytes_per_event": bytes_per_event,
+                         "traffic": (NCU_TRAFFIC["k_lazy"]["bytes_per_unit"] * events / steps
+                                     if NCU_TRAFFIC["k_lazy"]["bytes_per_unit"] else None),
+                         "traffic_note": NCU_TRAFFIC["k_lazy"]["source"] + ", scaled to this launch's events (random "
+                                         "32-byte sectors: ~2.5x the algorithmic bytes)",
+                         "kernel": "k_lazy<false>", "bytes_per_event": bytes_per_event,
                          "touched_channels_per_event": touched, "peak_source": how,
                          "note": "latency-bound: each event is a chain of dependent steps (slice minima, mailbox "
                                  "exchange, fire, touched channels, group minima); the bytes moved per event are "
