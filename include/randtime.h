@@ -296,7 +296,7 @@ int rt_philox(int64_t count, const uint32_t *ctr_dev, uint32_t key0, uint32_t ke
  * The paper groups the blocks of one trajectory into a "bundle" (Sec. 5); here
  * thousands of independent networks share one launch.  Each network is assigned
  * a mapping class by size: one thread per trajectory (M <= thread_max_m), one
- * warp (M <= warp_max_m), or one block of block_threads threads (M <= 8 *
+ * warp (M <= warp_max_m), or one block of block_threads threads (M <= 16 *
  * block_threads).  Work is a list of block-sized tasks (one block-class
  * trajectory, block_threads/32 warp-class or block_threads thread-class
  * trajectories), larger networks first, that persistent blocks take from an
@@ -316,7 +316,7 @@ typedef struct rt_batch_policy {
  * network i -> stream i; a run sharded over several GPUs passes each network's
  * global index so its trajectories equal the single-GPU run's.  policy may be NULL
  * (defaults 8 / 256 / 512 / 0).  All networks must live on the current device.
- * Networks too large for the block class (M > 8 * block_threads) return
+ * Networks too large for the block class (M > 16 * block_threads) return
  * RT_ERR_UNSUPPORTED. */
 int rt_batch_create(int32_t n_nets, const rt_network *const *nets, const uint32_t *stream_ids,
                     const rt_batch_policy *policy, rt_batch **out);

@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(512, 2) k_batch(const BatchArgs B) {
         case 1: block_trajectory<1, LL>(A, net, S, j, tf); break;
         case 2: block_trajectory<2, LL>(A, net, S, j, tf); break;
         case 4: block_trajectory<4, LL>(A, net, S, j, tf); break;
-        default: block_trajectory<8, LL>(A, net, S, j, tf); break;
+        case 8: block_trajectory<8, LL>(A, net, S, j, tf); break;
+        default: block_trajectory<16, LL>(A, net, S, j, tf); break;
       }
       continue;
     }
@@ -221,17 +222,17 @@ extern "C" int rt_batch_create(int32_t n_nets, const rt_network *const *nets, co
     int cls;
     if (M <= pol.thread_max_m && N <= 8) cls = CLS_THREAD;
     else if (M <= pol.warp_max_m) cls = CLS_WARP;
-    else if (M <= 8 * pol.block_threads) cls = CLS_BLOCK;
+    else if (M <= 16 * pol.block_threads) cls = CLS_BLOCK;
     else {
       delete b;
-      return set_error(RT_ERR_UNSUPPORTED, "network %d has %d reactions; this policy supports up to %d (8 per thread)",
-                       i, M, 8 * pol.block_threads);
+      return set_error(RT_ERR_UNSUPPORTED, "network %d has %d reactions; this policy supports up to %d (16 per thread)",
+                       i, M, 16 * pol.block_threads);
     }
     int R = 1;
     if (cls == CLS_WARP) R = M <= 32 ? 1 : M <= 64 ? 2 : M <= 128 ? 4 : 8;
     if (cls == CLS_BLOCK) {
       const int need = (M + pol.block_threads - 1) / pol.block_threads;
-      R = need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : 8;
+      R = need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : 16;
       b->maxM_block = std::max(b->maxM_block, M);
       b->maxN_block = std::max(b->maxN_block, N);
     }

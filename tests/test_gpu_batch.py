@@ -38,7 +38,8 @@ def check_against_oracle(items, batch, out, n_traj, max_events, seed):
 
 
 @pytest.mark.parametrize("policy", [dict(), dict(thread_max_m=4, warp_max_m=64, block_threads=256),
-                                    dict(thread_max_m=0, warp_max_m=0)])
+                                    dict(thread_max_m=0, warp_max_m=0),
+                                    dict(warp_max_m=64, block_threads=128)])  # up to 16 channels per thread
 def test_batch_bit_exact_per_network(policy):
     items, batch, x0, t_end = make_batch(60, 1200, seed=5, **policy)
     info = batch.info()
