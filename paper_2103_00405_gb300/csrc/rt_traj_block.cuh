@@ -41,7 +41,6 @@ struct BlockScratch {
   float *red_q;     // [warps] float upper bound of each warp's candidate's waiting time
   int *red_k2;      // [warps]
   double *buf;      // [B] (and the broadcast slots below)
-  long long *s_wc;  // candidate's exact waiting time
   double *s_amu;    // propensity of the fired channel
   double *s_E;      // the fired channel's new Exp(1) increment
   int *s_over;      // set if the fired reaction would leave the int32 range
@@ -58,8 +57,7 @@ __device__ inline BlockScratch carve_block_scratch(unsigned char *base, int M, i
   BlockScratch s;
   s.buf = (double *)base;
   s.red_w = (long long *)(s.buf + B);
-  s.s_wc = s.red_w + W;
-  s.s_amu = (double *)(s.s_wc + 1);
+  s.s_amu = (double *)(s.red_w + W);
   s.s_E = s.s_amu + 1;
   s.red_u = (float *)(s.s_E + 1);
   s.red_q = s.red_u + W;
