@@ -103,3 +103,25 @@ def test_rescaled_form_limits():
     big = api.Network(W.random_mass_action(60, 300, seed=94))
     with pytest.raises(L.RandtimeError):
         api.simulate(big, W.poisson_x0(60, 10, 1), 1.0, 4, **RES)  # M > 256
+
+
+def test_table3_workload_at_full_size_sampled():
+    """The benchmarked launches of Table 3's form: 2^18 Lotka-Volterra trajectories to t_end = 10 on
+    the thread mapping, and 16384 trajectories of the M = 64 gradient network to t_end = 5 on the warp
+    mapping; sampled trajectories against the oracle, bit for bit (the oracle re-runs each sampled
+    trajectory alone by its global id)."""
+    cfg = W.ensemble_configs(1 << 18)[0]
+    g = api.simulate(api.Network(cfg["net"]), cfg["x0"], cfg["t_end"], 1 << 18, seed=1, max_events=cfg["max_events"],
+                     mapping=L.RT_MAP_THREAD, **RES)
+    torch.cuda.synchronize()
+    for j in (0, 1, 4097, 100000, (1 << 18) - 1):
+        o = oracle.run(cfg["net"], cfg["x0"], cfg["t_end"], 1, seed=1, traj_offset=j, max_events=cfg["max_events"],
+                       **MODE)
+        assert_same(g, o, keys=("x_final", "n_events", "status", "t_last"), idx=slice(j, j + 1))
+    gc = W.grad_config(16384)
+    gg = api.simulate(api.Network(gc["net"]), gc["x0"], gc["t_end"], 16384, seed=1, max_events=10**8,
+                      mapping=L.RT_MAP_WARP, **RES)
+    torch.cuda.synchronize()
+    for j in (0, 31, 8191, 16383):
+        o = oracle.run(gc["net"], gc["x0"], gc["t_end"], 1, seed=1, traj_offset=j, max_events=10**8, **MODE)
+        assert_same(gg, o, keys=("x_final", "n_events", "status", "t_last"), idx=slice(j, j + 1))
