@@ -53,6 +53,7 @@ class Network:
         en = None if enabled is None else np.ascontiguousarray(enabled, dtype=np.uint8)
         if en is not None and en.shape != (self.M,):
             raise ValueError("enabled must have one entry per reaction")
+        torch.cuda.synchronize(self.device)  # the table is rewritten in place: no launch may still read it
         L.check(self.lib.rt_network_set_enabled(self.handle, None if en is None else en.ctypes.data_as(ctypes.c_void_p)),
                 "rt_network_set_enabled")
         return self
@@ -63,6 +64,7 @@ class Network:
         b = None if beta is None else np.ascontiguousarray(beta, dtype=np.float64)
         if b is not None and b.shape != (self.M,):
             raise ValueError("beta must have one entry per reaction")
+        torch.cuda.synchronize(self.device)  # the slopes are rewritten in place: no launch may still read them
         L.check(self.lib.rt_network_set_rate_slopes(self.handle, None if b is None else b.ctypes.data_as(ctypes.c_void_p)),
                 "rt_network_set_rate_slopes")
         return self
