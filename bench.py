@@ -772,8 +772,9 @@ def run_batched(args, ctx, steps, warmup):
                        "networks_this_rank": len(items),
                        "parallelism": ("networks split over %d ranks, longest processing time first"
                                        % ctx.world) if ctx.world > 1 else "1 GPU",
-                       "l2": "network arena ~%d MB re-read from L2/HBM; graph replays back to back"
-                             % int(sum(it.net.n_reactions for it in items) * 40 / 2**20)},
+                       "l2": "network tables ~%d MB (about 170 B per reaction: descriptors, rates, net changes, "
+                             "reader and dependent lists) read through L2; graph replays back to back"
+                             % int(sum(it.net.n_reactions for it in items) * 170 / 2**20)},
             "events_per_step": events_all / steps, "clocks": clocks, "gpu_launches": steps, "roofline": roof}
 
     if ctx.rank == 0:

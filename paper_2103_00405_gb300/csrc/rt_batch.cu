@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(512, 2) k_batch(const BatchArgs B) {
       const BNet bn = B.nets[ni];
       const RunArgs A = item_args(B, ni, bn);
       const BlockScratch S = carve_block_scratch(smem, B.maxM_block, B.maxN_block, BT);
-      const BlockNet net{bn.d.M, bn.d.N, bn.d.rdesc, bn.d.c, bn.d.vptr, bn.d.vlist, bn.d.sptr, bn.d.slist};
+      const BlockNet net{bn.d.M, bn.d.N, bn.d.rdesc, bn.d.c, bn.d.vptr, bn.d.vlist, bn.d.sptr, bn.d.slist,
+                         bn.d.dptr, bn.d.dlist};
       const int tf = isfinite(A.t_end) ? 1 : 0;
       switch (bn.R) {
         case 1: block_trajectory<1, LL>(A, net, S, j, tf); break;
@@ -288,6 +289,8 @@ extern "C" int rt_batch_create(int32_t n_nets, const rt_network *const *nets, co
     d.depw16 = g->dev.depw16 ? (const uint8_t *)(db + g->off_depw16) : nullptr;
     d.depw8 = g->dev.depw8 ? (const uint8_t *)(db + g->off_depw8) : nullptr;
     d.vdep = g->dev.vdep ? (const int4 *)(db + g->off_vdep) : nullptr;
+    d.dptr = g->dev.dptr ? (const int32_t *)(db + g->off_dptr) : nullptr;
+    d.dlist = g->dev.dptr ? (const int32_t *)(db + g->off_dlist) : nullptr;
     hn[i].d = d;
   }
   memcpy(host.data() + off_nets, hn.data(), sizeof(BNet) * n_nets);

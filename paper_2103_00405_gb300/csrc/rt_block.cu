@@ -17,7 +17,8 @@ template <int R, bool LL>
 __global__ void __launch_bounds__(512, 2) k_ens_block(const RunArgs A, const int tend_finite) {
   extern __shared__ __align__(16) unsigned char smem[];
   const BlockScratch S = carve_block_scratch(smem, A.net.M, A.net.N, blockDim.x);
-  const BlockNet net{A.net.M, A.net.N, A.net.rdesc, A.net.c, A.net.vptr, A.net.vlist, A.net.sptr, A.net.slist};
+  const BlockNet net{A.net.M, A.net.N, A.net.rdesc, A.net.c, A.net.vptr, A.net.vlist, A.net.sptr, A.net.slist,
+                     A.net.dptr, A.net.dlist};
   for (int64_t j = blockIdx.x; j < A.n_traj; j += gridDim.x) block_trajectory<R, LL>(A, net, S, j, tend_finite);
 }
 

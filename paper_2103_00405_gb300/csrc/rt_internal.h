@@ -36,7 +36,13 @@ struct DevNet {
   const int4 *vdep;        // [M][3] per reaction, when it fits (else null): its net change packed in
                            // 4 words (species << 8) | (delta & 0xFF), unused words 0; then for each
                            // changed species the begin and the length of its reader list in slist
+  const int32_t *dptr;     // [M+1] (M <= kDepListMaxM, else null) the channels whose propensity
+  const int32_t *dlist;    // reaction k's firing changes: dlist[dptr[k]..dptr[k+1]) (the reader
+                           // lists of its changed species, concatenated; repeats possible)
 };
+
+// Networks up to this many reactions get the per-reaction dependent lists (dptr/dlist).
+constexpr int kDepListMaxM = 8192;
 
 // Packed net-change word: species in the high 24 bits, delta (-128..127, never 0) in the low 8.
 __host__ __device__ inline int vpack_species(int w) { return (int)((unsigned)w >> 8); }
@@ -68,7 +74,7 @@ struct rt_network {
   std::vector<double> c_host;  // the network's rates (host copy)
   double *beta_dev = nullptr;  // rate slopes on the device (rt_network_set_rate_slopes), or null
   size_t off_depw = 0, off_depw16 = 0, off_depw8 = 0;
-  size_t off_vdep = 0;
+  size_t off_vdep = 0, off_dptr = 0, off_dlist = 0;
   rt::SmallNet small = {};  // filled when M <= kSmallM and N <= kSmallN
 };
 

@@ -207,6 +207,17 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
       }
     }
   }
+  // per reaction the channels its firing touches: the reader lists of its changed species,
+  // concatenated (small and mid-size networks; the block routine marks them from one list)
+  std::vector<int32_t> dptr, dlist;
+  if (M <= kDepListMaxM) {
+    dptr.assign((size_t)M + 1, 0);
+    for (int32_t k = 0; k < M; k++) {
+      for (int32_t i = vptr[k]; i < vptr[k + 1]; i++)
+        for (int32_t q = sptr[vlist[i].x]; q < sptr[vlist[i].x + 1]; q++) dlist.push_back(slist[q]);
+      dptr[(size_t)k + 1] = (int32_t)dlist.size();
+    }
+  }
   std::vector<double> cc(c, c + M);
   for (auto &x : cc)
     if (x == 0.0) x = 0.0;  // -0.0 -> +0.0 so propensities are never negative zero
@@ -226,6 +237,8 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
   g->off_depw16 = off; off = align_up(off + std::max<size_t>(1, depw16.size()), 256);
   g->off_depw8 = off; off = align_up(off + std::max<size_t>(1, depw8.size()), 256);
   g->off_vdep = off; off = align_up(off + sizeof(int4) * std::max<size_t>(1, vdep.size()), 256);
+  g->off_dptr = off; off = align_up(off + sizeof(int32_t) * std::max<size_t>(1, dptr.size()), 256);
+  g->off_dlist = off; off = align_up(off + sizeof(int32_t) * std::max<size_t>(1, dlist.size()), 256);
   g->arena_bytes = off;
   g->host_blob.assign(off, '\0');
   char *hb = &g->host_blob[0];
@@ -242,6 +255,8 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
   if (!depw16.empty()) memcpy(hb + g->off_depw16, depw16.data(), depw16.size());
   if (!depw8.empty()) memcpy(hb + g->off_depw8, depw8.data(), depw8.size());
   if (!vdep.empty()) memcpy(hb + g->off_vdep, vdep.data(), sizeof(int4) * vdep.size());
+  if (!dptr.empty()) memcpy(hb + g->off_dptr, dptr.data(), sizeof(int32_t) * dptr.size());
+  if (!dlist.empty()) memcpy(hb + g->off_dlist, dlist.data(), sizeof(int32_t) * dlist.size());
 
   cudaGetDevice(&g->device);
   cudaError_t e = cudaMalloc(&g->arena, g->arena_bytes);
@@ -274,6 +289,8 @@ extern "C" int rt_network_create(int32_t N, int32_t M, int64_t n_reac_nz, const 
   d.depw16 = M <= 128 ? (const uint8_t *)(db + g->off_depw16) : nullptr;
   d.depw8 = M <= 64 ? (const uint8_t *)(db + g->off_depw8) : nullptr;
   d.vdep = vdep.empty() ? nullptr : (const int4 *)(db + g->off_vdep);
+  d.dptr = dptr.empty() ? nullptr : (const int32_t *)(db + g->off_dptr);
+  d.dlist = dptr.empty() ? nullptr : (const int32_t *)(db + g->off_dlist);
   g->max_dependents = max_dep;
   g->n_dep_nz = dep_nz;
   if (M <= kSmallM && N <= kSmallN) {

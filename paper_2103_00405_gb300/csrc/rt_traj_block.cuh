@@ -28,6 +28,8 @@ struct BlockNet {
   const int2 *vl;
   const int *sptr;
   const int *slist;
+  const int *dptr;   // per reaction the channels its firing touches (or null: from sptr/slist)
+  const int *dlist;
 };
 
 // shared-memory scratch of one block trajectory
@@ -284,11 +286,18 @@ __device__ __forceinline__ void block_trajectory(const RunArgs &A, const BlockNe
         if ((nx > INT_MAX) | (nx < 0)) *S.s_over = 1;
         X[e.x] = (int)(uint32_t)((uint32_t)X[e.x] + (uint32_t)e.y);
       }
-      for (int i = vb; i < ve; ++i) {
-        const int s = net.vl[i].x;
-        for (int q = net.sptr[s] + tid; q < net.sptr[s + 1]; q += B) {
-          const int ch = net.slist[q];
+      if (net.dptr) {  // one list per reaction: two dependent loads instead of four
+        for (int q = net.dptr[bk] + tid; q < net.dptr[bk + 1]; q += B) {
+          const int ch = net.dlist[q];
           atomicOr(&S.bm[ch >> 5], 1u << (ch & 31));
+        }
+      } else {
+        for (int i = vb; i < ve; ++i) {
+          const int s = net.vl[i].x;
+          for (int q = net.sptr[s] + tid; q < net.sptr[s + 1]; q += B) {
+            const int ch = net.slist[q];
+            atomicOr(&S.bm[ch >> 5], 1u << (ch & 31));
+          }
         }
       }
       if (tid == B - 1) {
