@@ -19,15 +19,17 @@ their own disjoint blocks), and the int64 moment sums are all-reduced over ranks
   grad    -- M = 64, N = 16, 65536 trajectories to t_end = 5, forward with the
              log-likelihood + backward kernel (FP64-issue roofline), against the plain forward
   table3  -- the paper's own Table 3 formulation against Table 2's internal-time form on the
-             Lotka-Volterra model of Fig. 1, 2^18 trajectories to t_end = 10
+             Lotka-Volterra model of Fig. 1, 2^18 trajectories to t_end = 10, and on the
+             gradient network (M = 64) with a warp per trajectory
 
 Printed JSON: value = events/s of the whole job (sum over ranks of fired events / max
 over ranks of the timed device time); e2e = the same metric through api.simulate with
 inputs copied from pinned host memory and outputs copied back inside the timed region;
 roofline for the dominant kernel of each workload; cpu_baseline = the CPU oracle on
-the host cores over a bounded sample of the ensemble workload.
+the host cores over a bounded sample of the ensemble workload (and of the other configurations).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload all|ensemble|large|batched|grad]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload all|ensemble|large|large_tree|batched|grad|table3]
 """
 from __future__ import annotations
 
@@ -55,7 +57,7 @@ SAMPLE_DT = 0.01
 # is the rate measured by rt_fp64_probe on the same GPU at the start of the run; the
 # nominal figure is printed beside it.
 FP64_OP_NOMINAL = 0.625e12
-# DRAM bytes per unit of work of two roofline kernels, each from one ncu capture
+# DRAM bytes per unit of work of three roofline kernels, each from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch over the units it
 # processed).  A kernel changed since its capture must have its entry set to None.
 NCU_TRAFFIC = {
@@ -76,7 +78,7 @@ def parse(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="all",
                     choices=["all", "ensemble", "large", "large_tree", "batched", "grad", "table3"],
-                    help="all (default): the ensemble headline plus the large, batched and grad sub-records; "
+                    help="all (default): the ensemble headline plus the other workloads' sub-records; "
                          "one name: that workload alone as the line's headline (profiling captures)")
     ap.add_argument("--traj", type=int, default=1 << 20, help="ensemble: trajectories per network per step")
     ap.add_argument("--cpu-sample", type=int, default=1024, help="oracle trajectories per network")
