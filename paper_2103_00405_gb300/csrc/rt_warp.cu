@@ -65,6 +65,94 @@ __global__ void __launch_bounds__(kWarpBlock, R >= 8 ? 4 : 1)
 }
 
 // ---------------------------------------------------------------------------------
+// Shared steps of the warp-per-trajectory kernels below (channel k in lane k % 32, slot
+// k / 32; X of the trajectory in shared memory, read and written by the warp's lanes).
+// ---------------------------------------------------------------------------------
+
+// X = X0 (the warp's lanes); true if a count is negative (every lane gets the answer)
+__device__ __forceinline__ bool warp_load_x0(const RunArgs &A, int64_t j, int *X, int lane) {
+  const int N = A.net.N;
+  const int32_t *x0 = A.x0 + (A.per_traj_x0 ? j * (int64_t)N : 0);
+  bool badl = false;
+  for (int sp = lane; sp < N; sp += 32) {
+    const int v = x0[sp];
+    X[sp] = v;
+    badl |= v < 0;
+  }
+  const bool bad = __any_sync(0xFFFFFFFFu, badl);
+  __syncwarp();
+  return bad;
+}
+
+// grid point gidx from the current X (-1 where unknown), into the per-trajectory grid and/or the
+// moment sums
+__device__ __forceinline__ void warp_record(const RunArgs &A, int64_t j, const int *X, int lane, int64_t gidx,
+                                            bool known) {
+  const int N = A.net.N;
+  if (A.out.grid_dev) {
+    int32_t *gp = A.out.grid_dev + (j * A.G + gidx) * N;
+    for (int sp = lane; sp < N; sp += 32) gp[sp] = known ? X[sp] : -1;
+  }
+  if (!known || !A.out.grid_sum_dev) return;
+  for (int sp = lane; sp < N; sp += 32) {
+    const long long x = X[sp];
+    atomicAdd((unsigned long long *)(A.out.grid_sum_dev + gidx * N + sp), (unsigned long long)x);
+    if (A.out.grid_sumsq_dev)
+      atomicAdd((unsigned long long *)(A.out.grid_sumsq_dev + gidx * N + sp), (unsigned long long)(x * x));
+  }
+  if (lane == 0 && A.out.grid_count_dev) atomicAdd((unsigned long long *)(A.out.grid_count_dev + gidx), 1ull);
+}
+
+// would firing reaction kb push a count out of [0, INT32_MAX]? (every lane gets the answer)
+__device__ __forceinline__ bool warp_overflow(const DevNet &d, int kb, const int *X, int lane) {
+  bool over = false;
+  for (int i = d.vptr[kb] + lane; i < d.vptr[kb + 1]; i += 32) {
+    const int2 e = d.vlist[i];
+    const long long nx = (long long)X[e.x] + e.y;
+    over |= (nx > INT_MAX) | (nx < 0);
+  }
+  return __any_sync(0xFFFFFFFFu, over);
+}
+
+// X += v_kb (after every read of the pre-event X; the species of one reaction are distinct)
+__device__ __forceinline__ void warp_fire(const DevNet &d, int kb, int *X, int lane) {
+  __syncwarp();
+  for (int i = d.vptr[kb] + lane; i < d.vptr[kb + 1]; i += 32) {
+    const int2 e = d.vlist[i];
+    X[e.x] += e.y;
+  }
+  __syncwarp();
+}
+
+// the per-trajectory outputs after the run (internal times already final)
+template <int R>
+__device__ __forceinline__ void warp_write_outputs(const RunArgs &A, int64_t j, const int *X, int lane, bool bad,
+                                                   const double (&T)[R], const int32_t (&n)[R], double ll, int32_t ev,
+                                                   int status, double t) {
+  const int M = A.net.M, N = A.net.N;
+  if (A.out.t_internal_dev)
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (lane + 32 * r < M) A.out.t_internal_dev[j * M + lane + 32 * r] = T[r];
+  if (A.out.loglik_dev) {
+    const double sT = warp_sum_T_in_order<R, 32>(T, M, true);  // sum_k T_k in k order
+    if (lane == 0) A.out.loglik_dev[j] = bad ? __longlong_as_double(0x7FF8000000000000ll) : __dsub_rn(ll, sT);
+  }
+  if (A.out.counts_dev)
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (lane + 32 * r < M) A.out.counts_dev[j * M + lane + 32 * r] = n[r];
+  if (A.out.x_final_dev)
+    for (int sp = lane; sp < N; sp += 32) A.out.x_final_dev[j * N + sp] = X[sp];
+  trace_tail(A.out, j, ev, lane, 32);
+  if (lane == 0) {
+    if (A.out.n_events_dev) A.out.n_events_dev[j] = ev;
+    if (A.out.status_dev) A.out.status_dev[j] = status;
+    if (A.out.t_last_dev) A.out.t_last_dev[j] = t;
+  }
+}
+
+// ---------------------------------------------------------------------------------
 // Time-dependent rates c_k(t) = c_k (1 + beta_k t) (Sec. 6, Eq. 29) for networks of up to
 // 256 reactions: a warp per trajectory, channel k in lane k % 32, register slot k / 32.
 // Every waiting time is the root of its channel's own integral, computed exactly (the
@@ -85,15 +173,7 @@ __global__ void __launch_bounds__(kWarpBlock) k_ens_tdep_warp(const RunArgs A, c
   int *X = (int *)smem + (size_t)warp * N;
   auto xat = [&](int sp) { return X[sp]; };
   const uint64_t g = (uint64_t)(A.traj_offset + j);
-  const int32_t *x0 = A.x0 + (A.per_traj_x0 ? j * (int64_t)N : 0);
-  bool badl = false;
-  for (int sp = lane; sp < N; sp += 32) {
-    const int v = x0[sp];
-    X[sp] = v;
-    badl |= v < 0;
-  }
-  const bool bad = __any_sync(FULL, badl);
-  __syncwarp();
+  const bool bad = warp_load_x0(A, j, X, lane);
   double P[R], T[R], a[R], bt[R];
   int32_t n[R];
 #pragma unroll
@@ -114,20 +194,7 @@ __global__ void __launch_bounds__(kWarpBlock) k_ens_tdep_warp(const RunArgs A, c
   int32_t ev = 0;
   int64_t gi = 0;
   double next_g = 0.0;
-  auto record = [&](int64_t gidx, bool known) {
-    if (A.out.grid_dev) {
-      int32_t *gp = A.out.grid_dev + (j * A.G + gidx) * N;
-      for (int sp = lane; sp < N; sp += 32) gp[sp] = known ? X[sp] : -1;
-    }
-    if (!known || !A.out.grid_sum_dev) return;
-    for (int sp = lane; sp < N; sp += 32) {
-      const long long x = X[sp];
-      atomicAdd((unsigned long long *)(A.out.grid_sum_dev + gidx * N + sp), (unsigned long long)x);
-      if (A.out.grid_sumsq_dev)
-        atomicAdd((unsigned long long *)(A.out.grid_sumsq_dev + gidx * N + sp), (unsigned long long)(x * x));
-    }
-    if (lane == 0 && A.out.grid_count_dev) atomicAdd((unsigned long long *)(A.out.grid_count_dev + gidx), 1ull);
-  };
+  auto record = [&](int64_t gidx, bool known) { warp_record(A, j, X, lane, gidx, known); };
   if (!bad) {
     const int64_t tend_bits = dbits(A.t_end);
     for (;;) {
@@ -167,14 +234,7 @@ __global__ void __launch_bounds__(kWarpBlock) k_ens_tdep_warp(const RunArgs A, c
         status = RT_TRAJ_MAX_EVENTS;
         break;
       }
-      const int vb = d.vptr[kb], ve = d.vptr[kb + 1];
-      bool over = false;
-      for (int i = vb + lane; i < ve; i += 32) {
-        const int2 e = d.vlist[i];
-        const long long nx = (long long)X[e.x] + e.y;
-        over |= (nx > INT_MAX) | (nx < 0);
-      }
-      if (__any_sync(FULL, over)) {
+      if (warp_overflow(d, kb, X, lane)) {
         status = RT_TRAJ_OVERFLOW;
         break;
       }
@@ -193,12 +253,7 @@ __global__ void __launch_bounds__(kWarpBlock) k_ens_tdep_warp(const RunArgs A, c
       for (int r = 0; r < R; ++r)
         if (lane + 32 * r < M) T[r] = __dadd_rn(T[r], __dmul_rn(a[r], tdep_integral(bt[r], tprev, dmin)));
       if (LL && lane == 0) ll = __dadd_rn(ll, rt_ln(__dmul_rn(a_mu, __dadd_rn(1.0, __dmul_rn(b_mu, t)))));
-      __syncwarp();  // every read of the pre-event X is done
-      for (int i = vb + lane; i < ve; i += 32) {
-        const int2 e = d.vlist[i];
-        X[e.x] += e.y;  // the species of one reaction are distinct
-      }
-      __syncwarp();
+      warp_fire(d, kb, X, lane);
       if (lane == ol) {
         int32_t nmu = 0;
 #pragma unroll
@@ -228,27 +283,8 @@ __global__ void __launch_bounds__(kWarpBlock) k_ens_tdep_warp(const RunArgs A, c
       for (int r = 0; r < R; ++r)
         if (lane + 32 * r < M) T[r] = __dadd_rn(T[r], __dmul_rn(a[r], tdep_integral(bt[r], t, rest)));
     }
-    if (A.out.t_internal_dev)
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (lane + 32 * r < M) A.out.t_internal_dev[j * M + lane + 32 * r] = T[r];
-    if (A.out.loglik_dev) {
-      const double sT = warp_sum_T_in_order<R, 32>(T, M, true);  // sum_k T_k in k order
-      if (lane == 0) A.out.loglik_dev[j] = bad ? __longlong_as_double(0x7FF8000000000000ll) : __dsub_rn(ll, sT);
-    }
   }
-  if (A.out.counts_dev)
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-      if (lane + 32 * r < M) A.out.counts_dev[j * M + lane + 32 * r] = n[r];
-  if (A.out.x_final_dev)
-    for (int sp = lane; sp < N; sp += 32) A.out.x_final_dev[j * N + sp] = X[sp];
-  trace_tail(A.out, j, ev, lane, 32);
-  if (lane == 0) {
-    if (A.out.n_events_dev) A.out.n_events_dev[j] = ev;
-    if (A.out.status_dev) A.out.status_dev[j] = status;
-    if (A.out.t_last_dev) A.out.t_last_dev[j] = t;
-  }
+  warp_write_outputs<R>(A, j, X, lane, bad, T, n, ll, ev, status, t);
 }
 
 template <int R>
@@ -305,15 +341,7 @@ __global__ void __launch_bounds__(kWarpBlock) k_ens_rescaled_warp(const RunArgs 
   int *X = (int *)smem + (size_t)warp * N;
   auto xat = [&](int sp) { return X[sp]; };
   const uint64_t g = (uint64_t)(A.traj_offset + j);
-  const int32_t *x0 = A.x0 + (A.per_traj_x0 ? j * (int64_t)N : 0);
-  bool badl = false;
-  for (int sp = lane; sp < N; sp += 32) {
-    const int v = x0[sp];
-    X[sp] = v;
-    badl |= v < 0;
-  }
-  const bool bad = __any_sync(FULL, badl);
-  __syncwarp();
+  const bool bad = warp_load_x0(A, j, X, lane);
   double w[R], T[R], a[R];
   int32_t n[R];
 #pragma unroll
@@ -334,20 +362,7 @@ __global__ void __launch_bounds__(kWarpBlock) k_ens_rescaled_warp(const RunArgs 
   int32_t ev = 0;
   int64_t gi = 0;
   double next_g = 0.0;
-  auto record = [&](int64_t gidx, bool known) {
-    if (A.out.grid_dev) {
-      int32_t *gp = A.out.grid_dev + (j * A.G + gidx) * N;
-      for (int sp = lane; sp < N; sp += 32) gp[sp] = known ? X[sp] : -1;
-    }
-    if (!known || !A.out.grid_sum_dev) return;
-    for (int sp = lane; sp < N; sp += 32) {
-      const long long x = X[sp];
-      atomicAdd((unsigned long long *)(A.out.grid_sum_dev + gidx * N + sp), (unsigned long long)x);
-      if (A.out.grid_sumsq_dev)
-        atomicAdd((unsigned long long *)(A.out.grid_sumsq_dev + gidx * N + sp), (unsigned long long)(x * x));
-    }
-    if (lane == 0 && A.out.grid_count_dev) atomicAdd((unsigned long long *)(A.out.grid_count_dev + gidx), 1ull);
-  };
+  auto record = [&](int64_t gidx, bool known) { warp_record(A, j, X, lane, gidx, known); };
   if (!bad) {
     const int64_t tend_bits = dbits(A.t_end);
     for (;;) {
@@ -385,14 +400,7 @@ __global__ void __launch_bounds__(kWarpBlock) k_ens_rescaled_warp(const RunArgs 
         status = RT_TRAJ_MAX_EVENTS;
         break;
       }
-      const int vb = d.vptr[kb], ve = d.vptr[kb + 1];
-      bool over = false;
-      for (int i = vb + lane; i < ve; i += 32) {
-        const int2 e = d.vlist[i];
-        const long long nx = (long long)X[e.x] + e.y;
-        over |= (nx > INT_MAX) | (nx < 0);
-      }
-      if (__any_sync(FULL, over)) {
+      if (warp_overflow(d, kb, X, lane)) {
         status = RT_TRAJ_OVERFLOW;
         break;
       }
@@ -410,12 +418,7 @@ __global__ void __launch_bounds__(kWarpBlock) k_ens_rescaled_warp(const RunArgs 
         for (int r = 0; r < R; ++r)
           if (lane + 32 * r < M) T[r] = __dadd_rn(T[r], __dmul_rn(a[r], dmin));
       if (LL && lane == 0) ll = __dadd_rn(ll, rt_ln(a_mu));
-      __syncwarp();  // every read of the pre-event X is done
-      for (int i = vb + lane; i < ve; i += 32) {
-        const int2 e = d.vlist[i];
-        X[e.x] += e.y;  // the species of one reaction are distinct
-      }
-      __syncwarp();
+      warp_fire(d, kb, X, lane);
       double E = 0.0;
       if (lane == ol) {
         int32_t nmu = 0;
@@ -456,27 +459,8 @@ __global__ void __launch_bounds__(kWarpBlock) k_ens_rescaled_warp(const RunArgs 
       for (int r = 0; r < R; ++r)
         if (lane + 32 * r < M) T[r] = __dadd_rn(T[r], __dmul_rn(a[r], rest));
     }
-    if (A.out.t_internal_dev)
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (lane + 32 * r < M) A.out.t_internal_dev[j * M + lane + 32 * r] = T[r];
-    if (A.out.loglik_dev) {
-      const double sT = warp_sum_T_in_order<R, 32>(T, M, true);  // sum_k T_k in k order
-      if (lane == 0) A.out.loglik_dev[j] = bad ? __longlong_as_double(0x7FF8000000000000ll) : __dsub_rn(ll, sT);
-    }
   }
-  if (A.out.counts_dev)
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-      if (lane + 32 * r < M) A.out.counts_dev[j * M + lane + 32 * r] = n[r];
-  if (A.out.x_final_dev)
-    for (int sp = lane; sp < N; sp += 32) A.out.x_final_dev[j * N + sp] = X[sp];
-  trace_tail(A.out, j, ev, lane, 32);
-  if (lane == 0) {
-    if (A.out.n_events_dev) A.out.n_events_dev[j] = ev;
-    if (A.out.status_dev) A.out.status_dev[j] = status;
-    if (A.out.t_last_dev) A.out.t_last_dev[j] = t;
-  }
+  warp_write_outputs<R>(A, j, X, lane, bad, T, n, ll, ev, status, t);
 }
 
 template <int R>
