@@ -53,7 +53,7 @@ enum {
   RT_TRAJ_MAX_EVENTS = 1, /* max_events events fired */
   RT_TRAJ_ABSORBED = 2,   /* every propensity is zero: no event can ever fire */
   RT_TRAJ_OVERFLOW = 3,   /* the next event would push a count above INT32_MAX (not fired) */
-  RT_TRAJ_TIMEOUT = 4,    /* a bounded cross-block wait gave up (large-network mode) */
+  RT_TRAJ_TIMEOUT = 4,    /* a bounded cross-block wait gave up (bundle and tree mappings) */
   RT_TRAJ_BAD_X0 = 5      /* a negative initial count */
 };
 
@@ -224,6 +224,13 @@ int rt_workspace_bytes(const rt_network *net, const rt_run_params *params, const
  * With loglik/counts/t_internal outputs, T_k is advanced to t_end at the end
  * (when the run reached t_end or was absorbed) and the log-likelihood
  * sum_events ln a_mu - sum_k T_k (summed in k order) is written.
+ *
+ * params->form selects the form of the method (RT_FORM_*): the absolute-time form
+ * runs on RT_MAP_TREE only, Table 3's form on the thread (M <= 8) or warp (M <= 256)
+ * mapping; a network with rate slopes (rt_network_set_rate_slopes) runs the
+ * internal-time form on the thread (M <= 16) or warp (M <= 256) mapping; forbidden
+ * channels (rt_network_set_enabled) are honoured by every mapping and form.  Other
+ * combinations return RT_ERR_UNSUPPORTED before anything is enqueued.
  *
  * x0 values are checked on the device (negative -> RT_TRAJ_BAD_X0).  workspace
  * must be at least rt_workspace_bytes() (may be NULL when that is 0).
