@@ -51,7 +51,7 @@ struct __align__(32) ChanRec {
   double a;  // propensity since s
 };
 
-constexpr int kPostWarp = kLazyWarps - 1;         // the root, its prefetch and the posts (no global stores)
+constexpr int kPostWarp = kLazyWarps - 1;         // the slice minimum, the posts and the L2 prefetch (no global stores)
 constexpr int kDrawTid = (kLazyWarps - 2) * 32;    // lane 0 of warp 14 updates the fired channel
 
 // a mailbox slot: the posting CTA's slice minimum for one event
